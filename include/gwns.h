@@ -1,0 +1,206 @@
+/*
+ * gwns.h -- C ABI of libgwns, a GB300 (sm_103a) implementation of the batched
+ * acceptance-walk nested sampler for gravitational-wave inference described in
+ * arXiv 2509.04336 ("Gravitational-wave inference at GPU speed: a bilby-like nested
+ * sampling kernel within blackjax-ns").
+ *
+ * What the library computes (the paper's statement of the problem):
+ *   evidence     Z = int L(d|theta) pi(theta) dtheta                     (Eq. 2, Sec. 2.1)
+ *   posterior    P(theta|d) = L pi / Z, as weighted dead + live points   (Eq. 1; Sec. 3.2 weights)
+ *   likelihood   ln L = -1/2 sum_det <d - h_det | d - h_det>,
+ *                <a|b> = 4 df Re sum_k conj(a_k) b_k / S_n(f_k)          (Sec. 3.3)
+ *   sampler      batched nested sampling: delete the k lowest live points, L* = max of
+ *                the deleted, evolve k constrained chains in parallel     (Sec. 2.2.3)
+ *   inner kernel differential-evolution acceptance walk in the unit cube,
+ *                accepting iff L > L*, walk length tuned per batch        (Sec. 3.1, Sec. 3.2)
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (NS_OK) on success, a negative NS_E* code on failure, NS_WMAXMCMC (> 0)
+ *     as a warning.  No C++ exception crosses the ABI.  ns_last_error() returns a
+ *     message for the last failure of a handle (or of ns_init when handle is NULL).
+ *   - Physical parameter vectors theta are 11 doubles in this order:
+ *       chirp mass [Msun, detector frame], mass ratio q = m2/m1 <= 1, chi_1, chi_2,
+ *       luminosity distance [Mpc], theta_jn [rad], psi [rad], phase phi_c [rad],
+ *       geocentre coalescence time t_c [s, relative to the segment reference],
+ *       right ascension [rad], declination [rad].
+ *   - Unit-cube vectors u hold the D sampled (non-FIXED) parameters in the same order.
+ *   - Arrays are row-major and densely packed.  ptr_kind says whether the caller's
+ *     pointers are host (NS_PTR_HOST, pageable or pinned) or device (NS_PTR_DEVICE)
+ *     memory.  Caller buffers are borrowed for the duration of the call only; with
+ *     device pointers the work is enqueued on `stream` and the call returns after
+ *     enqueueing (the caller synchronises); with host pointers the call blocks.
+ *   - stream == NULL means the handle's own stream.
+ *   - The library owns every buffer it allocates; ns_free releases them.
+ *   - One handle per host thread; a handle is bound to the device given to ns_init.
+ */
+#ifndef GWNS_H
+#define GWNS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GWNS_N_PARAMS 11
+#define GWNS_MAX_DET 4
+#define GWNS_MAX_EVENTS 256
+
+/* status codes */
+#define NS_OK 0
+#define NS_EINVAL (-1)      /* bad argument or configuration                          */
+#define NS_ECUDA (-2)       /* a CUDA runtime call failed                             */
+#define NS_ENOMEM (-3)      /* device or host allocation failed                       */
+#define NS_ENONFINITE (-4)  /* non-finite input (theta, data, PSD) or result           */
+#define NS_ETIMEOUT (-5)    /* a device loop hit its iteration/clock budget            */
+#define NS_ESTATE (-6)      /* call not valid in the current state (e.g. run finished) */
+#define NS_EIO (-7)         /* checkpoint file could not be written or read            */
+#define NS_WMAXMCMC 1       /* warning: a walk batch reached maxmcmc steps with no     */
+                            /* accepted move for some walker (its start is returned)   */
+
+/* prior kinds (Table 1) */
+#define NS_PRIOR_UNIFORM 0   /* x = lo + u (hi - lo)                                   */
+#define NS_PRIOR_POWERLAW 1  /* density ~ x^alpha on [lo, hi], alpha != -1             */
+#define NS_PRIOR_SINE 2      /* density ~ sin x on [lo, hi] within [0, pi]              */
+#define NS_PRIOR_COSINE 3    /* density ~ cos x on [lo, hi] within [-pi/2, pi/2]        */
+#define NS_PRIOR_FIXED 4     /* held at `value`, not sampled                            */
+
+#define NS_WAVEFORM_TAYLORF2 0      /* 3.5PN aligned-spin TaylorF2, zero above f_ISCO  */
+#define NS_WAVEFORM_PHENOMD_FORM 1  /* IMRPhenomD-form inspiral-merger-ringdown        */
+
+#define NS_PREC_FP64 0   /* every step in FP64 (the plain walk)                              */
+#define NS_PREC_MIXED 1  /* FP32 amplitude and inner products with compensated sums;           */
+                         /* FP64-accurate phase and its reduction; FP64 lnL assembly, evidence */
+
+#define NS_TERM_DLOGZ 0           /* stop when ln(Z + L_max X) - ln Z < term_value (Sec. 4.1.1)   */
+#define NS_TERM_FRAC_REMAINING 1  /* stop when L_mean X < term_value * Z (Sec. 4.2)              */
+
+#define NS_PTR_HOST 0
+#define NS_PTR_DEVICE 1
+
+typedef struct ns_prior {
+    int32_t kind;      /* NS_PRIOR_*                                  */
+    int32_t periodic;  /* nonzero: wrap u into [0, 1) in the walk      */
+    double lo, hi;     /* support                                      */
+    double alpha;      /* power-law index (NS_PRIOR_POWERLAW)          */
+    double value;      /* NS_PRIOR_FIXED value                         */
+} ns_prior;
+
+/* Sampler settings of one event (Sec. 3.2; values of Sec. 4.1.1 and Sec. 4.2). */
+typedef struct ns_config {
+    ns_prior prior[GWNS_N_PARAMS];
+    int32_t n_live;       /* live points                                            */
+    int32_t num_delete;   /* k, points deleted and replaced per batch (1 <= k < n_live) */
+    int32_t naccept;      /* target accepted steps per walk                         */
+    int32_t maxmcmc;      /* cap on the walk length                                 */
+    double delay;         /* sequential smoothing of the walk-length update; < 0 means
+                             naccept - 1.  The batch uses delay_k with
+                             delay_k/(delay_k+1) = (delay/(delay+1))^k              */
+    int32_t use_ratio;    /* nonzero: sample ln L + 1/2 sum <d|d> (likelihood ratio)  */
+    int32_t term_kind;    /* NS_TERM_*                                              */
+    double term_value;    /* dlogZ threshold or evidence fraction                   */
+    int32_t precision;    /* NS_PREC_*; the same for every event of a handle        */
+    int32_t waveform;     /* NS_WAVEFORM_*; the same for every event of a handle    */
+    int32_t max_iter;     /* hard cap on batches (0: 1000000)                       */
+    int32_t n_steps0;     /* first walk length (0: ceil(naccept / 0.25))            */
+    uint64_t seed;        /* Philox key word 0; key word 1 is the event index      */
+} ns_config;
+
+/* One detector's data.  Pointers are HOST arrays of n_bins doubles, copied by ns_init. */
+typedef struct ns_detector {
+    double vertex[3];     /* Earth-fixed position [m]                               */
+    double x_arm[3];      /* unit vector of the x arm                               */
+    double y_arm[3];      /* unit vector of the y arm                               */
+    const double* d_re;   /* Re d(f_k) [1/Hz]                                       */
+    const double* d_im;   /* Im d(f_k) [1/Hz]                                       */
+    const double* psd;    /* one-sided S_n(f_k) [1/Hz], > 0                          */
+} ns_detector;
+
+/* One event: data on the grid f_k = f_min + k df, k = 0 .. n_bins-1. */
+typedef struct ns_event {
+    int32_t n_det;        /* 1 .. GWNS_MAX_DET                                      */
+    int32_t n_bins;       /* >= 1                                                   */
+    double f_min;         /* [Hz] > 0                                               */
+    double df;            /* [Hz] > 0 (1 / segment duration)                        */
+    double gmst;          /* Greenwich sidereal angle of the event [rad]           */
+    ns_detector det[GWNS_MAX_DET];
+} ns_event;
+
+/* Progress of one event after ns_step. */
+typedef struct ns_progress {
+    int64_t iterations;   /* batches completed                                      */
+    int64_t n_like;       /* likelihood evaluations so far                          */
+    double log_z;         /* ln Z of the dead points so far                         */
+    double dlogz;         /* ln(Z + L_max X) - ln Z                                 */
+    double log_x;         /* expected ln X of the live set                          */
+    double lnl_star;      /* threshold of the last batch                            */
+    double mean_accept;   /* mean accepted steps per walker, last batch             */
+    int32_t n_steps;      /* walk length of the next batch                          */
+    int32_t done;         /* termination reached                                    */
+} ns_progress;
+
+typedef struct ns_handle ns_handle;
+
+/* Create a sampler for n_events events on CUDA device `device`.  cfg and ev are
+ * arrays of n_events.  Copies and preprocesses all inputs (whitening, basis tables,
+ * prefix sums), allocates the live/dead stores and draws the initial live points
+ * (Sec. 2.2.1: n_live draws from the prior).  On failure *out is NULL and
+ * ns_last_error(NULL) describes the problem. */
+int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, int device, ns_handle** out);
+
+/* Detector strain of the waveform model for n parameter vectors (the projection of
+ * Sec. 3.3 / Sec. 4.1.1 network): h_re, h_im are [n][n_det][n_bins] in physical units
+ * (1/Hz), FP64.  theta is [n][11]. */
+int ns_waveform(ns_handle* h, int event, const double* theta, int n,
+                double* h_re, double* h_im, int ptr_kind, void* stream);
+
+/* ln L (or ln Lambda under use_ratio) of n parameter vectors theta [n][11]
+ * (Sec. 3.3), computed in the handle's precision.  lnl is [n]. */
+int ns_likelihood_batch(ns_handle* h, int event, const double* theta, int n,
+                        double* lnl, int ptr_kind, void* stream);
+
+/* One walk batch of the inner kernel (Sec. 3.1): n walkers start at u0 [n][D] with
+ * ln L lnl0 [n] and take n_steps DE steps against the survivor set live_u [n_live_pts][D],
+ * accepting iff ln L > lnl_star.  Random numbers come from Philox4x64-10 with key
+ * (seed, event) and counters (step, walker_offset + w, iteration, tag), so a call is a
+ * pure function of its arguments.  Outputs: u_out [n][D], lnl_out [n], n_accept [n],
+ * n_like [n] (likelihood calls; out-of-bounds proposals are rejected without a call).
+ * n_live_pts >= 2.  Returns NS_WMAXMCMC when a walker accepted nothing. */
+int ns_walk_batch(ns_handle* h, int event, const double* live_u, int n_live_pts,
+                  const double* u0, const double* lnl0, double lnl_star,
+                  int n, int n_steps, int64_t iteration, int64_t walker_offset,
+                  double* u_out, double* lnl_out, int32_t* n_accept, int32_t* n_like,
+                  int ptr_kind, void* stream);
+
+/* Run up to max_batches batches of the sampler on every unfinished event (Sec. 2.2.3,
+ * Sec. 3.2): deletion, evidence update, walk, insertion, walk-length retune and the
+ * termination test all run on the device.  progress is [n_events] (may be NULL).
+ * Returns NS_OK when it ran; progress[e].done reports termination. */
+int ns_step(ns_handle* h, int max_batches, ns_progress* progress);
+
+/* Final evidence of an event: the dead points plus the final live points, each with
+ * weight L_i X / n_live.  log_z_err is the standard deviation of ln Z over replays
+ * with shrinkage factors t ~ Beta(n_i, 1); info_h is the information H. */
+int ns_evidence(ns_handle* h, int event, double* log_z, double* log_z_err,
+                double* info_h, int64_t* n_like);
+
+/* Posterior samples of an event (dead then final live points): theta_out [cap][11]
+ * physical parameters and logw_out [cap] normalised log weights (Eq. 1).  *n_out is
+ * the number of points available; at most cap are written.  Host pointers. */
+int ns_posterior(ns_handle* h, int event, double* theta_out, double* logw_out,
+                 int64_t cap, int64_t* n_out);
+
+/* Checkpoint / resume of the whole sampler state (live sets, dead stores, evidence
+ * accumulators, walk lengths, iteration counters).  A resumed run continues the
+ * same Philox streams and so replays bit-identically. */
+int ns_state_save(ns_handle* h, const char* path);
+int ns_state_load(ns_handle* h, const char* path);
+
+void ns_free(ns_handle* h);
+const char* ns_last_error(ns_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWNS_H */

@@ -1,0 +1,82 @@
+// api_internal.h -- the handle behind the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gwns.h"
+#include "gwns_internal.h"
+
+namespace gwns {
+
+constexpr int kMaxLive = 4096;     // live points per event (one CTA sorts them in shared memory)
+
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Device-resident nested-sampling state of one event.  The batch kernels read and write
+// it in place, so a captured graph replays batches without host round trips.
+struct NsState {
+  double log_x, log_z, lnl_star, dlogz, mean_accept, lnl_max, delay_k, term_value;
+  int64_t n_dead, n_like, iteration, max_iter, dead_cap;
+  int32_t n_live, k, D, n_steps, naccept, maxmcmc, term_kind, done, zero_accept, overflow;
+  uint64_t key0, key1;
+  double* live_u;      // [n_live][D]
+  double* live_lnl;    // [n_live]
+  double* surv_u;      // [n_live - k][D]
+  double* w_u0;        // [k][D]
+  double* w_lnl0;      // [k]
+  double* w_uo;        // [k][D]
+  double* w_lo;        // [k]
+  int32_t* w_na;       // [k]
+  int32_t* w_nl;       // [k]
+  int32_t* slot;       // [k]
+  double* dead_u;      // [dead_cap][D]
+  double* dead_lnl;    // [dead_cap]
+  double* dead_logw;   // [dead_cap]
+  int32_t* dead_nlive; // [dead_cap]
+};
+
+struct EventHost {
+  ns_config cfg;
+  int n_det = 0, n_bins = 0, n_dim = 0;
+  EventDev dev;
+  double* d_basis64 = nullptr;
+  double2* d_z64 = nullptr;
+  float2* d_z32 = nullptr;
+  double* d_hh_prefix = nullptr;
+  NsState ns;            // host mirror of the device pointers and static fields
+};
+
+}  // namespace gwns
+
+struct ns_handle {
+  int device = 0;
+  int precision = 0;
+  int waveform = 0;
+  int max_det = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<gwns::EventHost> events;
+  gwns::EventDev* d_events = nullptr;
+  int32_t* d_status = nullptr;
+  gwns::Scratch scratch_in, scratch_out, scratch_map;
+  // nested sampling
+  gwns::NsState* d_ns = nullptr;
+  gwns::WalkTask* d_tasks = nullptr;
+  int32_t* d_blk_task = nullptr;
+  int32_t* d_blk_local = nullptr;
+  int n_walk_blocks = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_batches = 0;
+  std::vector<gwns::NsState> host_ns;   // last progress snapshot
+  std::string err;
+};
+
+int set_error(ns_handle* h, int code, const char* fmt, ...);
+int cuda_fail(ns_handle* h, cudaError_t e, const char* what);
+int ensure_scratch(ns_handle* h, gwns::Scratch& s, size_t bytes);
+int nested_init(ns_handle* h);
+void nested_free(ns_handle* h);

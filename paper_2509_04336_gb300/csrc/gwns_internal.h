@@ -1,0 +1,50 @@
+// gwns_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gwns_model.cuh"
+
+namespace gwns {
+
+constexpr int kThreads = 128;   // threads per walker CTA
+
+// Per-event descriptor of one walk batch, read by the walk kernel.  The nested-sampling
+// kernels rewrite lnl_star, n_steps and iteration between batches, so a captured graph
+// replays without host involvement.
+struct WalkTask {
+  const double* surv;      // [n_s][D] survivors
+  const double* u0;        // [n][D] starts
+  const double* lnl0;      // [n]
+  double* u_out;           // [n][D]
+  double* lnl_out;         // [n]
+  int32_t* n_acc;          // [n]
+  int32_t* n_like;         // [n]
+  double lnl_star;
+  int64_t iteration;
+  int64_t walker_offset;
+  uint64_t key0, key1;
+  int32_t n_s;
+  int32_t n;
+  int32_t n_steps;
+  int32_t done;
+  int32_t event;           // index into the event table
+  int32_t pad;
+};
+
+// Launch wrappers (kernels.cu).  Every wrapper returns the launch error.
+cudaError_t launch_likelihood(int precision, int n_det, const EventDev* d_ev, const double* d_theta,
+                              int n, double* d_lnl, int32_t* d_status, cudaStream_t s);
+cudaError_t launch_waveform(int n_det, const EventDev* d_ev, const double* d_theta, int n, int n_bins,
+                            double* d_hre, double* d_him, cudaStream_t s);
+cudaError_t launch_unit_likelihood(int precision, int n_det, const EventDev* d_ev, const double* d_u, int n,
+                                   double* d_lnl, cudaStream_t s);
+cudaError_t launch_unit_to_theta(const EventDev* d_ev, const double* d_u, int64_t n, double* d_theta,
+                                 cudaStream_t s);
+// Block b walks walker blk_local[b] of task blk_task[b].
+cudaError_t launch_walk(int precision, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
+                        const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks,
+                        cudaStream_t s);
+
+}  // namespace gwns

@@ -1,0 +1,331 @@
+// gwns_model.cuh -- device-side model of the frequency-domain GW likelihood (Sec. 3.3)
+// and of the unit-cube prior transforms (Sec. 3.4, Table 1) used by every kernel.
+//
+// Factorisation used on the GPU (algebraically identical to the plain definition):
+//   h_det(f_k) = K f_k^(-7/6) P_det exp(-2 pi i Phi_det(f_k)),   P_det = F+ (1+ci^2)/2 - i Fx ci
+//   Phi_det(f) = sum_j C_j g_j(f) + phase0 + (t_c + dt_det) f        [cycles]
+//   g = (f^-5/3, f^-1, f^-2/3, f^-1/3, f^1/3, f^2/3, ln f, f^1/3 ln f): the TaylorF2 PN
+//   series  3/(128 eta v^5) sum_k (a_k + a^l_k ln v) v^k  with v^k = (pi M)^(k/3) f^(k/3)
+//   and ln v = (ln(pi M) + ln f)/3, regrouped by powers of f.  The g_j are per-bin
+//   constants shared by every walker; only the C_j depend on theta.
+//   <d|h_det> = Re[K P_det S_det],   S_det = sum_k z_k exp(-2 pi i Phi_det(f_k)),
+//   z_k = 4 df conj(d_k) f_k^(-7/6) / S_n(f_k)      (per-bin constant)
+//   <h|h>_det = K^2 |P_det|^2 sum_{k < k_end} 4 df f_k^(-7/3) / S_n(f_k)   (prefix sums)
+//   ln L = -1/2 (sum <d|d> - 2 sum <d|h> + sum <h|h>);  use_ratio: sum <d|h> - 1/2 sum <h|h>.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace gwns {
+
+constexpr int kParams = 11;
+constexpr int kMaxDet = 4;
+constexpr int kMaxDim = 11;
+constexpr int kBasis = 8;
+
+// SI constants: exact c, IAU 2015 nominal solar mass parameter, IAU parsec.
+constexpr double kC = 299792458.0;
+constexpr double kGMsun = 1.32712440018e20;
+constexpr double kMsunS = kGMsun / (kC * kC * kC);
+constexpr double kMpcM = 3.085677581491367e22;
+constexpr double kPi = 3.141592653589793;
+constexpr double kEulerGamma = 0.5772156649015329;
+constexpr double kLn4 = 1.3862943611198906;
+constexpr double kSix15 = 14.696938456699069;   // 6^(3/2)
+constexpr double kAmp0 = 0.21278751013966343;   // sqrt(5/24) pi^(-2/3)
+
+enum PriorKind { kUniform = 0, kPowerLaw = 1, kSine = 2, kCosine = 3, kFixed = 4 };
+
+// One prior entry with its inverse-CDF constants precomputed on the host.
+//   uniform:  x = lo + u*w                     (w = hi - lo)
+//   powerlaw: x = (A + u*B)^(1/(alpha+1))      (A = lo^(alpha+1), B = hi^(alpha+1) - A, e = alpha+1)
+//   sine:     cos x = A - u*B                  (A = cos lo, B = cos lo - cos hi)
+//   cosine:   sin x = A + u*B                  (A = sin lo, B = sin hi - sin lo)
+//   fixed:    x = value (cosv = cos value, sinv = sin value)
+struct PriorDev {
+  int kind;
+  int periodic;
+  double lo, hi, w, A, B, e, value, cosv, sinv;
+};
+
+// Device copy of one event and its sampler configuration.
+struct EventDev {
+  int n_det, n_bins, n_dim, use_ratio;
+  double f_min, df, gmst;
+  double dd_total;                     // sum_det <d|d>
+  double vertex[kMaxDet][3], xarm[kMaxDet][3], yarm[kMaxDet][3];
+  PriorDev prior[kParams];
+  int dim_param[kMaxDim];              // physical index of each sampled dimension
+  const double* basis64;               // [n_bins][kBasis]
+  const double2* z64;                  // [n_det][n_bins]
+  const float2* z32;                   // [n_det][n_bins]
+  const double* hh_prefix;             // [n_det][n_bins] inclusive prefix sums of 4 df f^-7/3 / S
+};
+
+// Per-walker constants of one likelihood evaluation.
+struct WalkerParams {
+  double C[kBasis];
+  double phase0;
+  double tau[kMaxDet];
+  double kp_re[kMaxDet], kp_im[kMaxDet];
+  double hh;
+  int k_end;
+  int pad;
+};
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Salmon, Moraes, Dror & Shaw 2011: 10 rounds of multiply-xor with a Weyl key schedule.
+struct Philox4 { uint64_t v[4]; };
+
+__device__ __forceinline__ Philox4 philox4x64(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                              uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    uint64_t n0 = hi1 ^ c1 ^ k0;
+    uint64_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  Philox4 r; r.v[0] = c0; r.v[1] = c1; r.v[2] = c2; r.v[3] = c3;
+  return r;
+}
+
+// floor(x * n / 2^64)
+__device__ __forceinline__ uint64_t rand_index(uint64_t x, uint64_t n) { return __umul64hi(x, n); }
+// uniform on (0, 1): ((x >> 12) + 1/2) / 2^52
+__device__ __forceinline__ double rand_open_unit(uint64_t x) {
+  return __dmul_rn(__dadd_rn((double)(x >> 12), 0.5), 2.220446049250313e-16);
+}
+
+// ---------------------------------------------------------------- prior transform
+// Physical theta [11] from unit-cube u [D], plus cos(theta_jn), sin(dec), cos(dec), which
+// the sine / cosine priors give without inverse trigonometry.
+__device__ inline void unit_to_theta(const EventDev& ev, const double* u, double* th,
+                                     double* cos_iota, double* sin_dec, double* cos_dec) {
+  int d = 0;
+  double ci = 0.0, sd = 0.0, cd = 1.0;
+  bool have_ci = false, have_dec = false;
+  for (int i = 0; i < kParams; ++i) {
+    const PriorDev& p = ev.prior[i];
+    double x;
+    if (p.kind == kFixed) {
+      x = p.value;
+      if (i == 5) { ci = p.cosv; have_ci = true; }
+      if (i == 10) { sd = p.sinv; cd = p.cosv; have_dec = true; }
+    } else {
+      double v = u[d++];
+      if (p.kind == kUniform) {
+        x = __dadd_rn(p.lo, __dmul_rn(v, p.w));
+      } else if (p.kind == kPowerLaw) {
+        double y = __dadd_rn(p.A, __dmul_rn(v, p.B));
+        x = (p.e == 3.0) ? cbrt(y) : pow(y, 1.0 / p.e);
+      } else if (p.kind == kSine) {
+        double c = __dsub_rn(p.A, __dmul_rn(v, p.B));
+        c = fmin(1.0, fmax(-1.0, c));
+        x = acos(c);
+        if (i == 5) { ci = c; have_ci = true; }
+      } else {  // cosine
+        double s = __dadd_rn(p.A, __dmul_rn(v, p.B));
+        s = fmin(1.0, fmax(-1.0, s));
+        x = asin(s);
+        if (i == 10) { sd = s; cd = sqrt(fmax(0.0, (1.0 - s) * (1.0 + s))); have_dec = true; }
+      }
+    }
+    th[i] = x;
+  }
+  if (!have_ci) ci = cos(th[5]);
+  if (!have_dec) { sincos(th[10], &sd, &cd); }
+  *cos_iota = ci; *sin_dec = sd; *cos_dec = cd;
+}
+
+// ---------------------------------------------------------------- TaylorF2 setup
+// 3.5PN aligned-spin TaylorF2 phase coefficients a_k, a^l_k (non-spinning terms of
+// Buonanno et al. 2009; spin terms in the chi_s, chi_a, delta form of Khan et al. 2016).
+__device__ inline void taylorf2_pn_coeffs(double eta, double delta, double chis, double chia,
+                                          double a[8], double al[8]) {
+  const double pi = kPi;
+  double e2 = eta * eta, e3 = e2 * eta;
+  a[0] = 1.0; a[1] = 0.0;
+  a[2] = 3715.0 / 756.0 + 55.0 * eta / 9.0;
+  a[3] = -16.0 * pi + 113.0 / 3.0 * delta * chia + (113.0 / 3.0 - 76.0 * eta / 3.0) * chis;
+  a[4] = 15293365.0 / 508032.0 + 27145.0 * eta / 504.0 + 3085.0 * e2 / 72.0
+       + (-405.0 / 8.0 + 200.0 * eta) * chia * chia - 405.0 / 4.0 * delta * chia * chis
+       + (-405.0 / 8.0 + 5.0 * eta / 2.0) * chis * chis;
+  double gso = (732985.0 / 2268.0 - 24260.0 * eta / 81.0 - 340.0 * e2 / 9.0) * chis
+             + (732985.0 / 2268.0 + 140.0 * eta / 9.0) * delta * chia;
+  a[5] = 38645.0 * pi / 756.0 - 65.0 * pi * eta / 9.0 - gso;
+  a[6] = 11583231236531.0 / 4694215680.0 - 6848.0 * kEulerGamma / 21.0 - 640.0 * pi * pi / 3.0
+       + (-15737765635.0 / 3048192.0 + 2255.0 * pi * pi / 12.0) * eta
+       + 76055.0 * e2 / 1728.0 - 127825.0 * e3 / 1296.0 - 6848.0 / 21.0 * kLn4
+       + pi * 2270.0 / 3.0 * delta * chia + pi * (2270.0 / 3.0 - 520.0 * eta) * chis;
+  a[7] = pi * (77096675.0 / 254016.0 + 378515.0 * eta / 1512.0 - 74045.0 * e2 / 756.0)
+       + (-25150083775.0 / 3048192.0 + 10566655595.0 * eta / 762048.0 - 1042165.0 * e2 / 3024.0
+          + 5345.0 * e3 / 36.0) * chis
+       + (-25150083775.0 / 3048192.0 + 26804935.0 * eta / 6048.0 - 1985.0 * e2 / 48.0) * delta * chia;
+  for (int k = 0; k < 8; ++k) al[k] = 0.0;
+  al[5] = 3.0 * a[5];
+  al[6] = -6848.0 / 21.0;
+}
+
+// Number of bins with f_k <= f_cut (f_k = f_min + k df, exactly as the grid is defined).
+__device__ inline int bins_below(double f_min, double df, int n_bins, double f_cut) {
+  if (!(f_cut >= f_min)) return 0;
+  double x = floor((f_cut - f_min) / df);
+  long k = (long)fmin(x, (double)n_bins);
+  while (k + 1 <= n_bins - 1 && f_min + df * (double)(k + 1) <= f_cut) ++k;
+  while (k >= 0 && (k > n_bins - 1 || f_min + df * (double)k > f_cut)) --k;
+  return (int)(k + 1);
+}
+
+// Antenna pattern (F+, Fx) and arrival delay of one detector.  F+ = D:e+, Fx = D:ex with
+// D = (x x^T - y y^T)/2 reduce to projections of the arms on the wave axes X, Y.
+__device__ inline void detector_response(const EventDev& ev, int det, double sp, double cp,
+                                         double sdec, double cdec, double ss, double cs,
+                                         double* fp, double* fc, double* dt) {
+  // theta = pi/2 - dec: cos theta = sin dec, sin theta = cos dec
+  double ct = sdec, st = cdec;
+  double X0 = sp * cs - ss * cp * ct, X1 = -(cp * cs + ss * sp * ct), X2 = ss * st;
+  double Y0 = -sp * ss - cs * cp * ct, Y1 = cp * ss - cs * sp * ct, Y2 = st * cs;
+  const double* x = ev.xarm[det];
+  const double* y = ev.yarm[det];
+  double xX = x[0] * X0 + x[1] * X1 + x[2] * X2, xY = x[0] * Y0 + x[1] * Y1 + x[2] * Y2;
+  double yX = y[0] * X0 + y[1] * X1 + y[2] * X2, yY = y[0] * Y0 + y[1] * Y1 + y[2] * Y2;
+  *fp = 0.5 * (xX * xX - xY * xY - yX * yX + yY * yY);
+  *fc = xX * xY - yX * yY;
+  const double* r = ev.vertex[det];
+  double n0 = cdec * cp, n1 = cdec * sp, n2 = sdec;
+  *dt = -(r[0] * n0 + r[1] * n1 + r[2] * n2) / kC;
+}
+
+// Per-walker constants for theta (with cos iota, sin dec, cos dec supplied).
+__device__ inline void taylorf2_setup(const EventDev& ev, const double* th, double ci, double sdec,
+                                      double cdec, WalkerParams& p) {
+  double mc = th[0], q = th[1], chi1 = th[2], chi2 = th[3], dl = th[4];
+  double psi = th[6], phic = th[7], tc = th[8], ra = th[9];
+  double eta = q / ((1.0 + q) * (1.0 + q));
+  double mtot = mc * pow(eta, -0.6);
+  double delta = (1.0 - q) / (1.0 + q);
+  double chis = 0.5 * (chi1 + chi2), chia = 0.5 * (chi1 - chi2);
+  double piM = kPi * (mtot * kMsunS);
+  double f_cut = 1.0 / (kSix15 * piM);
+  p.k_end = bins_below(ev.f_min, ev.df, ev.n_bins, f_cut);
+
+  double a[8], al[8];
+  taylorf2_pn_coeffs(eta, delta, chis, chia, a, al);
+  double lpm = log(piM);
+  double c1 = cbrt(piM);
+  double ci1 = 1.0 / c1;
+  double ci2 = ci1 * ci1, ci3 = ci2 * ci1, ci5 = ci3 * ci2;
+  double pre = 3.0 / (256.0 * kPi * eta);      // 3/(128 eta) / (2 pi): cycles
+  p.C[0] = pre * ci5 * a[0];
+  p.C[1] = pre * ci3 * a[2];
+  p.C[2] = pre * ci2 * a[3];
+  p.C[3] = pre * ci1 * a[4];
+  p.C[4] = pre * c1 * (a[6] + al[6] * lpm / 3.0);
+  p.C[5] = pre * c1 * c1 * a[7];
+  p.C[6] = pre * al[5] / 3.0;
+  p.C[7] = pre * c1 * al[6] / 3.0;
+  p.phase0 = pre * (a[5] + al[5] * lpm / 3.0) - phic / kPi - 0.125;
+
+  // restricted amplitude K = sqrt(5/24) pi^(-2/3) (G Mc/c^3)^(5/6) / (d_L/c)
+  double mcs = mc * kMsunS;
+  double K = kAmp0 * sqrt(mcs) * cbrt(mcs) * kC / (dl * kMpcM);
+
+  double sp, cp, ss, cs;
+  sincos(ra - ev.gmst, &sp, &cp);
+  sincos(psi, &ss, &cs);
+  double ap = 0.5 * (1.0 + ci * ci);
+  double hh = 0.0;
+  for (int det = 0; det < ev.n_det; ++det) {
+    double fp, fc, dt;
+    detector_response(ev, det, sp, cp, sdec, cdec, ss, cs, &fp, &fc, &dt);
+    double pre_re = fp * ap, pre_im = -fc * ci;
+    p.kp_re[det] = K * pre_re;
+    p.kp_im[det] = K * pre_im;
+    p.tau[det] = tc + dt;
+    double psum = p.k_end > 0 ? ev.hh_prefix[(size_t)det * ev.n_bins + p.k_end - 1] : 0.0;
+    hh += K * K * (pre_re * pre_re + pre_im * pre_im) * psum;
+  }
+  p.hh = hh;
+}
+
+// ---------------------------------------------------------------- per-bin accumulation
+struct AccF64 {
+  double re[kMaxDet], im[kMaxDet];
+  __device__ void zero() { for (int i = 0; i < kMaxDet; ++i) { re[i] = 0.0; im[i] = 0.0; } }
+};
+
+// Kahan-compensated FP32 accumulator.
+struct AccF32 {
+  float re[kMaxDet], im[kMaxDet], cre[kMaxDet], cim[kMaxDet];
+  __device__ void zero() {
+    for (int i = 0; i < kMaxDet; ++i) { re[i] = 0.f; im[i] = 0.f; cre[i] = 0.f; cim[i] = 0.f; }
+  }
+};
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  float y = x - c;
+  float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// FP64 path: every operation in double precision.
+template <int NDET>
+__device__ __forceinline__ void bin_accumulate_f64(const EventDev& ev, const WalkerParams& p, int k,
+                                                   AccF64& acc) {
+  const double* g = ev.basis64 + (size_t)k * kBasis;
+  double phi = p.phase0;
+#pragma unroll
+  for (int j = 0; j < kBasis; ++j) phi = fma(p.C[j], g[j], phi);
+  double f = ev.f_min + ev.df * (double)k;
+#pragma unroll
+  for (int det = 0; det < NDET; ++det) {
+    double ph = fma(p.tau[det], f, phi);
+    double r = ph - rint(ph);
+    double s, c;
+    sincospi(2.0 * r, &s, &c);
+    double2 z = ev.z64[(size_t)det * ev.n_bins + k];
+    // z * exp(-2 pi i r) = (zr c + zi s) + i (zi c - zr s)
+    acc.re[det] += z.x * c + z.y * s;
+    acc.im[det] += z.y * c - z.x * s;
+  }
+}
+
+// Mixed path: FP64 phase and its reduction, FP32 sincos and compensated FP32 sums.
+template <int NDET>
+__device__ __forceinline__ void bin_accumulate_mixed(const EventDev& ev, const WalkerParams& p, int k,
+                                                     AccF32& acc) {
+  const double* g = ev.basis64 + (size_t)k * kBasis;
+  double phi = p.phase0;
+#pragma unroll
+  for (int j = 0; j < kBasis; ++j) phi = fma(p.C[j], g[j], phi);
+  double f = ev.f_min + ev.df * (double)k;
+#pragma unroll
+  for (int det = 0; det < NDET; ++det) {
+    double ph = fma(p.tau[det], f, phi);
+    float r = (float)(ph - rint(ph));
+    float s, c;
+    sincospif(2.0f * r, &s, &c);
+    float2 z = ev.z32[(size_t)det * ev.n_bins + k];
+    kahan_add(acc.re[det], acc.cre[det], fmaf(z.x, c, z.y * s));
+    kahan_add(acc.im[det], acc.cim[det], fmaf(z.y, c, -z.x * s));
+  }
+}
+
+// ln L from the reduced sums S_det (FP64 assembly).
+__device__ inline double assemble_lnl(const EventDev& ev, const WalkerParams& p, const double* s_re,
+                                      const double* s_im) {
+  double dh = 0.0;
+  for (int det = 0; det < ev.n_det; ++det) dh += p.kp_re[det] * s_re[det] - p.kp_im[det] * s_im[det];
+  if (ev.use_ratio) return dh - 0.5 * p.hh;
+  return -0.5 * (ev.dd_total - 2.0 * dh + p.hh);
+}
+
+}  // namespace gwns

@@ -1,0 +1,249 @@
+"""Python binding of libgwns (include/gwns.h): argument marshalling only.
+
+Every function has the name and argument order of its C counterpart.  Arrays may be
+torch tensors (CUDA tensors are passed as device pointers on the current torch stream,
+CPU tensors as host pointers) or numpy arrays (host pointers).  Loading fails loudly when
+the shared library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgwns.so")
+
+N_PARAMS = 11
+MAX_DET = 4
+
+NS_OK, NS_EINVAL, NS_ECUDA, NS_ENOMEM, NS_ENONFINITE, NS_ETIMEOUT, NS_ESTATE, NS_EIO = 0, -1, -2, -3, -4, -5, -6, -7
+NS_WMAXMCMC = 1
+NS_PTR_HOST, NS_PTR_DEVICE = 0, 1
+STATUS_NAMES = {0: "NS_OK", -1: "NS_EINVAL", -2: "NS_ECUDA", -3: "NS_ENOMEM", -4: "NS_ENONFINITE",
+                -5: "NS_ETIMEOUT", -6: "NS_ESTATE", -7: "NS_EIO", 1: "NS_WMAXMCMC"}
+
+
+class ns_prior(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("periodic", C.c_int32), ("lo", C.c_double), ("hi", C.c_double),
+                ("alpha", C.c_double), ("value", C.c_double)]
+
+
+class ns_config(C.Structure):
+    _fields_ = [("prior", ns_prior * N_PARAMS), ("n_live", C.c_int32), ("num_delete", C.c_int32),
+                ("naccept", C.c_int32), ("maxmcmc", C.c_int32), ("delay", C.c_double),
+                ("use_ratio", C.c_int32), ("term_kind", C.c_int32), ("term_value", C.c_double),
+                ("precision", C.c_int32), ("waveform", C.c_int32), ("max_iter", C.c_int32),
+                ("n_steps0", C.c_int32), ("seed", C.c_uint64)]
+
+
+class ns_detector(C.Structure):
+    _fields_ = [("vertex", C.c_double * 3), ("x_arm", C.c_double * 3), ("y_arm", C.c_double * 3),
+                ("d_re", C.POINTER(C.c_double)), ("d_im", C.POINTER(C.c_double)), ("psd", C.POINTER(C.c_double))]
+
+
+class ns_event(C.Structure):
+    _fields_ = [("n_det", C.c_int32), ("n_bins", C.c_int32), ("f_min", C.c_double), ("df", C.c_double),
+                ("gmst", C.c_double), ("det", ns_detector * MAX_DET)]
+
+
+class ns_progress(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("n_like", C.c_int64), ("log_z", C.c_double), ("dlogz", C.c_double),
+                ("log_x", C.c_double), ("lnl_star", C.c_double), ("mean_accept", C.c_double),
+                ("n_steps", C.c_int32), ("done", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ("ns_init", "ns_waveform", "ns_likelihood_batch", "ns_walk_batch", "ns_step", "ns_evidence",
+           "ns_posterior", "ns_state_save", "ns_state_load", "ns_free", "ns_last_error")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgwns.so (once).  Raises if it is missing: build it with paper_2509_04336_gb300.build."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgwns.so not found at {path}; run paper_2509_04336_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, I, D, V = C.c_void_p, C.c_int, C.c_double, C.c_void_p
+    lib.ns_init.argtypes = [C.POINTER(ns_config), C.POINTER(ns_event), I, I, C.POINTER(C.c_void_p)]
+    lib.ns_waveform.argtypes = [P, I, P, I, P, P, I, V]
+    lib.ns_likelihood_batch.argtypes = [P, I, P, I, P, I, V]
+    lib.ns_walk_batch.argtypes = [P, I, P, I, P, P, D, I, I, C.c_int64, C.c_int64, P, P, P, P, I, V]
+    lib.ns_step.argtypes = [P, I, C.POINTER(ns_progress)]
+    lib.ns_evidence.argtypes = [P, I, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                C.POINTER(C.c_int64)]
+    lib.ns_posterior.argtypes = [P, I, P, P, C.c_int64, C.POINTER(C.c_int64)]
+    lib.ns_state_save.argtypes = [P, C.c_char_p]
+    lib.ns_state_load.argtypes = [P, C.c_char_p]
+    lib.ns_free.argtypes = [P]
+    lib.ns_free.restype = None
+    lib.ns_last_error.argtypes = [P]
+    lib.ns_last_error.restype = C.c_char_p
+    for name in EXPORTS[:-2]:
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class GwnsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code, handle, allow_warning=False):
+    if code == NS_OK or (allow_warning and code == NS_WMAXMCMC):
+        return code
+    msg = _lib.ns_last_error(handle)
+    raise GwnsError(code, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(address, ptr_kind, stream) of a torch tensor or numpy array."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, NS_PTR_HOST, None
+    import torch
+    if not a.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    if a.is_cuda:
+        return a.data_ptr(), NS_PTR_DEVICE, torch.cuda.current_stream(a.device).cuda_stream
+    return a.data_ptr(), NS_PTR_HOST, None
+
+
+def _same_kind(*arrays):
+    ptrs = [_ptr(a) for a in arrays]
+    kinds = {p[1] for p in ptrs}
+    if len(kinds) != 1:
+        raise ValueError("all arrays of a call must be host or all device")
+    return ptrs
+
+
+# ---------------------------------------------------------------- marshalling helpers
+def make_config(w: synth.Workload, priors=None, *, precision=None, max_iter=0, n_steps0=0, delay=-1.0,
+                seed=None) -> ns_config:
+    c = ns_config()
+    pri = w.priors if priors is None else priors
+    for i, p in enumerate(pri):
+        c.prior[i] = ns_prior(p.kind, 1 if p.periodic else 0, p.lo, p.hi, p.alpha, p.value)
+    c.n_live, c.num_delete, c.naccept, c.maxmcmc = w.n_live, w.num_delete, w.naccept, w.maxmcmc
+    c.delay = delay
+    c.use_ratio = 1 if w.use_ratio else 0
+    c.term_kind, c.term_value = w.term_kind, w.term_value
+    c.precision = w.precision if precision is None else precision
+    c.waveform = w.waveform
+    c.max_iter, c.n_steps0 = max_iter, n_steps0
+    c.seed = w.seed if seed is None else seed
+    return c
+
+
+def make_event(ev: synth.Event):
+    """ns_event for a synth.Event; returns (struct, keepalive) -- keep both alive until ns_init returns."""
+    e = ns_event()
+    e.n_det, e.n_bins, e.f_min, e.df, e.gmst = len(ev.detectors), ev.n_bins, ev.f_min, ev.df, ev.gmst
+    keep = []
+    for i, d in enumerate(ev.detectors):
+        re = np.ascontiguousarray(d.data.real, dtype=np.float64)
+        im = np.ascontiguousarray(d.data.imag, dtype=np.float64)
+        ps = np.ascontiguousarray(d.psd, dtype=np.float64)
+        keep += [re, im, ps]
+        det = e.det[i]
+        for j in range(3):
+            det.vertex[j], det.x_arm[j], det.y_arm[j] = d.vertex[j], d.x_arm[j], d.y_arm[j]
+        det.d_re = re.ctypes.data_as(C.POINTER(C.c_double))
+        det.d_im = im.ctypes.data_as(C.POINTER(C.c_double))
+        det.psd = ps.ctypes.data_as(C.POINTER(C.c_double))
+    return e, keep
+
+
+# ---------------------------------------------------------------- entry points
+def ns_init(configs, events, device: int = 0):
+    """configs: list of ns_config; events: list of synth.Event or ns_event.  Returns the handle."""
+    lib = load()
+    n = len(configs)
+    cfg_arr = (ns_config * n)(*configs)
+    ev_arr = (ns_event * n)()
+    keep = []
+    for i, ev in enumerate(events):
+        if isinstance(ev, ns_event):
+            ev_arr[i] = ev
+        else:
+            s, k = make_event(ev)
+            ev_arr[i] = s
+            keep.append(k)
+    h = C.c_void_p()
+    code = lib.ns_init(cfg_arr, ev_arr, n, device, C.byref(h))
+    if code != NS_OK:
+        raise GwnsError(code, lib.ns_last_error(None).decode())
+    return h
+
+
+def ns_waveform(h, event: int, theta, h_re, h_im):
+    (pt, kind, st), (pr, _, _), (pi, _, _) = _same_kind(theta, h_re, h_im)
+    return _check(_lib.ns_waveform(h, event, pt, theta.shape[0], pr, pi, kind, st), h)
+
+
+def ns_likelihood_batch(h, event: int, theta, lnl):
+    (pt, kind, st), (pl, _, _) = _same_kind(theta, lnl)
+    return _check(_lib.ns_likelihood_batch(h, event, pt, theta.shape[0], pl, kind, st), h)
+
+
+def ns_walk_batch(h, event: int, live_u, u0, lnl0, lnl_star: float, n_steps: int, iteration: int,
+                  walker_offset: int, u_out, lnl_out, n_accept, n_like):
+    ps = _same_kind(live_u, u0, lnl0, u_out, lnl_out, n_accept, n_like)
+    kind, st = ps[0][1], ps[0][2]
+    code = _lib.ns_walk_batch(h, event, ps[0][0], live_u.shape[0], ps[1][0], ps[2][0], float(lnl_star),
+                              u0.shape[0], n_steps, iteration, walker_offset, ps[3][0], ps[4][0], ps[5][0],
+                              ps[6][0], kind, st)
+    return _check(code, h, allow_warning=True)
+
+
+def ns_step(h, max_batches: int, n_events: int = 1):
+    prog = (ns_progress * n_events)()
+    code = _check(_lib.ns_step(h, max_batches, prog), h, allow_warning=True)
+    return code, [p.as_dict() for p in prog]
+
+
+def ns_evidence(h, event: int = 0):
+    lz, err, info = C.c_double(), C.c_double(), C.c_double()
+    nl = C.c_int64()
+    _check(_lib.ns_evidence(h, event, C.byref(lz), C.byref(err), C.byref(info), C.byref(nl)), h)
+    return lz.value, err.value, info.value, nl.value
+
+
+def ns_posterior(h, event: int = 0, cap: int | None = None):
+    n = C.c_int64()
+    _check(_lib.ns_posterior(h, event, None, None, 0, C.byref(n)), h)
+    m = n.value if cap is None else min(cap, n.value)
+    th = np.zeros((m, N_PARAMS))
+    lw = np.zeros(m)
+    _check(_lib.ns_posterior(h, event, th.ctypes.data, lw.ctypes.data, m, C.byref(n)), h)
+    return th, lw
+
+
+def ns_state_save(h, path: str):
+    return _check(_lib.ns_state_save(h, path.encode()), h)
+
+
+def ns_state_load(h, path: str):
+    return _check(_lib.ns_state_load(h, path.encode()), h)
+
+
+def ns_free(h):
+    if h is not None and _lib is not None:
+        _lib.ns_free(h)
+
+
+def ns_last_error(h=None) -> str:
+    msg = load().ns_last_error(h)
+    return msg.decode() if msg else ""

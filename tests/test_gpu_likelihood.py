@@ -1,0 +1,114 @@
+"""CUDA path vs the oracle: waveform element by element, ln L per parameter vector."""
+import numpy as np
+import pytest
+
+from oracle import likelihood as L
+from paper_2509_04336_gb300 import gwns, synth
+
+from _util import event, priors, prior_draws, oracle_lnl
+
+pytestmark = pytest.mark.gpu
+
+# FP64 path: same arithmetic up to rounding order (phase regrouped by powers of f).
+TOL_FP64 = 1e-11
+# Mixed path: ln L within 1e-6 of |ln L| (FP32 sums; FP64 phase reduced before an FP32 sincos).
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2509_04336_gb300 import build
+    build.build()
+
+
+def handle(w, ev, precision):
+    cfg = gwns.make_config(w, priors(w, ev), precision=precision)
+    return gwns.ns_init([cfg], [ev])
+
+
+@pytest.mark.parametrize("name", ["four_param_2det_taylorf2", "bbh11_3det_4s_taylorf2"])
+def test_waveform_elementwise(name):
+    w, ev = event(name)
+    h = handle(w, ev, synth.PREC_FP64)
+    try:
+        _, th = prior_draws(w, ev, 6, 11)
+        th = np.vstack([ev.theta_inj, th])
+        nd = len(ev.detectors)
+        hr = np.zeros((th.shape[0], nd, ev.n_bins))
+        hi = np.zeros_like(hr)
+        gwns.ns_waveform(h, 0, np.ascontiguousarray(th), hr, hi)
+        for i in range(th.shape[0]):
+            for d in range(nd):
+                want = L.project(ev, d, th[i], w.waveform)
+                got = hr[i, d] + 1j * hi[i, d]
+                scale = np.max(np.abs(want))
+                assert np.all((want == 0) == (got == 0)), "cutoff bin differs"
+                assert np.max(np.abs(got - want)) <= 1e-10 * scale
+    finally:
+        gwns.ns_free(h)
+
+
+@pytest.mark.parametrize("name,precision,tol", [
+    ("four_param_2det_taylorf2", synth.PREC_FP64, TOL_FP64),
+    ("four_param_2det_taylorf2", synth.PREC_MIXED, TOL_MIXED),
+    ("bbh11_3det_4s_taylorf2", synth.PREC_FP64, TOL_FP64),
+    ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED, TOL_MIXED),
+])
+def test_likelihood_parity(name, precision, tol):
+    w, ev = event(name)
+    h = handle(w, ev, precision)
+    try:
+        _, th = prior_draws(w, ev, 96, 5)
+        th = np.ascontiguousarray(np.vstack([ev.theta_inj, th]))
+        got = np.zeros(th.shape[0])
+        gwns.ns_likelihood_batch(h, 0, th, got)
+        want = oracle_lnl(w, ev, th)
+        err = np.abs(got - want)
+        # zero-noise truth has ln L = 0: an absolute floor of tol * SNR^2 / 2 there
+        scale = np.maximum(np.abs(want), 0.5 * w.snr ** 2)
+        assert np.all(err <= tol * scale), f"max rel err {np.max(err / scale):.3e}"
+    finally:
+        gwns.ns_free(h)
+
+
+def test_likelihood_device_pointers_and_edge_cases():
+    import torch
+    w, ev = event("bbh11_3det_4s_taylorf2")
+    h = handle(w, ev, synth.PREC_MIXED)
+    try:
+        _, th = prior_draws(w, ev, 5, 9)
+        # masses giving a cutoff below f_min: no active bin, h = 0, ln L = -<d|d>/2
+        heavy = ev.theta_inj.copy(); heavy[0] = 400.0
+        th = np.vstack([th, heavy])
+        t = torch.tensor(th, device="cuda", dtype=torch.float64)
+        out = torch.zeros(th.shape[0], device="cuda", dtype=torch.float64)
+        gwns.ns_likelihood_batch(h, 0, t, out)
+        torch.cuda.synchronize()
+        want = oracle_lnl(w, ev, th)
+        assert np.allclose(out.cpu().numpy(), want, rtol=TOL_MIXED, atol=0)
+        # empty batch is a no-op
+        gwns.ns_likelihood_batch(h, 0, np.zeros((0, 11)), np.zeros(0))
+        # non-finite theta is reported, not evaluated
+        bad = th[:2].copy(); bad[1, 3] = np.nan
+        with pytest.raises(gwns.GwnsError) as e:
+            gwns.ns_likelihood_batch(h, 0, np.ascontiguousarray(bad), np.zeros(2))
+        assert e.value.code == gwns.NS_ENONFINITE
+    finally:
+        gwns.ns_free(h)
+
+
+def test_likelihood_ragged_bins_small_event():
+    # 23 bins: fewer than one CTA's threads, and a ragged tail.
+    w, ev = event("bbh11_3det_4s_taylorf2", f_max=25.5)
+    assert ev.n_bins == 23
+    for prec, tol in ((synth.PREC_FP64, TOL_FP64), (synth.PREC_MIXED, TOL_MIXED)):
+        h = handle(w, ev, prec)
+        try:
+            _, th = prior_draws(w, ev, 17, 3)
+            th = np.ascontiguousarray(th)
+            got = np.zeros(17)
+            gwns.ns_likelihood_batch(h, 0, th, got)
+            want = oracle_lnl(w, ev, th)
+            assert np.all(np.abs(got - want) <= tol * np.maximum(np.abs(want), 1.0))
+        finally:
+            gwns.ns_free(h)
