@@ -241,6 +241,7 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
     return set_error(nullptr, NS_EINVAL, "waveform %d is not available in this build", cfg[0].waveform);
   cudaError_t e0 = cudaSetDevice(device);
   if (e0 != cudaSuccess) return set_error(nullptr, NS_ECUDA, "cudaSetDevice(%d): %s", device, cudaGetErrorString(e0));
+  cudaGetLastError();   // a stale error of an earlier call must not be reported here
   ns_handle* h = new ns_handle();
   h->device = device;
   h->precision = cfg[0].precision;
@@ -290,6 +291,7 @@ extern "C" int ns_waveform(ns_handle* h, int event, const double* theta, int n, 
   if (ptr_kind != NS_PTR_HOST && ptr_kind != NS_PTR_DEVICE) return set_error(h, NS_EINVAL, "bad ptr_kind");
   if (n == 0) return NS_OK;
   cudaSetDevice(h->device);
+  cudaGetLastError();
   EventHost& E = h->events[event];
   const EventDev* d_ev = h->d_events + event;
   cudaStream_t s = pick_stream(h, stream);
@@ -324,6 +326,7 @@ extern "C" int ns_likelihood_batch(ns_handle* h, int event, const double* theta,
   if (ptr_kind != NS_PTR_HOST && ptr_kind != NS_PTR_DEVICE) return set_error(h, NS_EINVAL, "bad ptr_kind");
   if (n == 0) return NS_OK;
   cudaSetDevice(h->device);
+  cudaGetLastError();
   EventHost& E = h->events[event];
   const EventDev* d_ev = h->d_events + event;
   cudaStream_t s = pick_stream(h, stream);
@@ -366,6 +369,7 @@ extern "C" int ns_walk_batch(ns_handle* h, int event, const double* live_u, int 
   if (std::isnan(lnl_star)) return set_error(h, NS_ENONFINITE, "lnl_star is NaN");
   if (n == 0) return NS_OK;
   cudaSetDevice(h->device);
+  cudaGetLastError();
   EventHost& E = h->events[event];
   const int D = E.n_dim;
   cudaStream_t s = pick_stream(h, stream);

@@ -21,7 +21,7 @@ struct Scratch {
 // it in place, so a captured graph replays batches without host round trips.
 struct NsState {
   double log_x, log_z, lnl_star, dlogz, mean_accept, lnl_max, delay_k, term_value;
-  int64_t n_dead, n_like, iteration, max_iter, dead_cap;
+  int64_t n_dead, n_like, iteration, max_iter, dead_cap, n_bins_eval;
   int32_t n_live, k, D, n_steps, naccept, maxmcmc, term_kind, done, zero_accept, overflow;
   uint64_t key0, key1;
   double* live_u;      // [n_live][D]
@@ -34,6 +34,7 @@ struct NsState {
   int32_t* w_na;       // [k]
   int32_t* w_nl;       // [k]
   int32_t* slot;       // [k]
+  int64_t* w_nb;       // [k] active bins evaluated per walker
   double* dead_u;      // [dead_cap][D]
   double* dead_lnl;    // [dead_cap]
   double* dead_logw;   // [dead_cap]
@@ -71,6 +72,9 @@ struct ns_handle {
   int n_walk_blocks = 0;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_batches = 0;
+  std::vector<cudaEvent_t> walk_events;  // [2 * batches in the graph]: start, end of each walk
+  double walk_ms = 0.0;
+  int64_t kernel_launches = 0;
   std::vector<gwns::NsState> host_ns;   // last progress snapshot
   std::string err;
 };

@@ -21,6 +21,7 @@ struct WalkTask {
   double* lnl_out;         // [n]
   int32_t* n_acc;          // [n]
   int32_t* n_like;         // [n]
+  int64_t* n_bins;         // [n] active bins evaluated per walker (may be null)
   double lnl_star;
   int64_t iteration;
   int64_t walker_offset;

@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(const EventDev* __restri
   if (threadIdx.x < D) u[threadIdx.x] = T.u0[(size_t)j * D + threadIdx.x];
   double lnl = T.lnl0[j];
   int n_acc = 0, n_like = 0;
+  int64_t n_bins = 0;
   const double de_scale = 2.38 / sqrt(2.0 * (double)D);
   __syncthreads();
   for (int t = 0; t < n_steps; ++t) {
@@ -275,6 +276,7 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(const EventDev* __restri
       if (threadIdx.x == 0) {
         double v = assemble_lnl(ev, P, s_re, s_im);
         ++n_like;
+        n_bins += P.k_end;
         if (v > lnl_star) {
           for (int d = 0; d < D; ++d) u[d] = prop[d];
           lnl = v;
@@ -289,6 +291,7 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(const EventDev* __restri
     T.lnl_out[j] = lnl;
     T.n_acc[j] = n_acc;
     T.n_like[j] = n_like;
+    if (T.n_bins) T.n_bins[j] = n_bins;
   }
 }
 

@@ -200,9 +200,10 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
   NsState& S = states[blockIdx.x];
   if (S.done) return;
   const int k = S.k, D = S.D, n = S.n_live, tid = threadIdx.x;
-  double acc = 0.0, calls = 0.0, zero = 0.0;
+  double acc = 0.0, calls = 0.0, zero = 0.0, bins = 0.0;
   for (int j = tid; j < k; j += kSelThreads) {
     int s = S.slot[j];
+    bins += (double)S.w_nb[j];
     for (int d = 0; d < D; ++d) S.live_u[(size_t)s * D + d] = S.w_uo[(size_t)j * D + d];
     S.live_lnl[s] = S.w_lo[j];
     acc += (double)S.w_na[j];
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
   const double tot_acc = block_sum(acc, buf);
   const double tot_calls = block_sum(calls, buf);
   const double n_zero = block_sum(zero, buf);
+  const double tot_bins = block_sum(bins, buf);
   __syncthreads();
   double mx = -INFINITY;
   for (int i = tid; i < n; i += kSelThreads) mx = fmax(mx, S.live_lnl[i]);
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
     double mean_acc = tot_acc / (double)k;
     S.mean_accept = mean_acc;
     S.n_like += (int64_t)tot_calls;
+    S.n_bins_eval += (int64_t)tot_bins;
     if (n_zero > 0.0) S.zero_accept = 1;
     // walk-length retune (batch-scaled delay)
     double ns = (double)S.n_steps;
@@ -379,14 +382,20 @@ int ensure_dead_capacity(ns_handle* h, int batches) {
   return NS_OK;
 }
 
-int enqueue_batch(ns_handle* h) {
+int enqueue_batch(ns_handle* h, int b) {
   const int ne = (int)h->events.size();
   select_kernel<<<ne, kSelThreads, 0, h->stream>>>(h->d_ns, h->d_tasks);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "select launch");
+  // inside stream capture a plain event record is only a dependency marker; the external
+  // flag makes it an event-record node that timestamps every replay
+  if ((e = cudaEventRecordWithFlags(h->walk_events[2 * b], h->stream, cudaEventRecordExternal)) != cudaSuccess)
+    return cuda_fail(h, e, "event");
   e = launch_walk(h->precision, h->max_det, h->d_events, h->d_tasks, h->d_blk_task, h->d_blk_local,
                   h->n_walk_blocks, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "walk launch");
+  if ((e = cudaEventRecordWithFlags(h->walk_events[2 * b + 1], h->stream, cudaEventRecordExternal)) != cudaSuccess)
+    return cuda_fail(h, e, "event");
   insert_kernel<<<ne, kSelThreads, 0, h->stream>>>(h->d_ns, h->d_tasks);
   e = cudaGetLastError();
   return e == cudaSuccess ? NS_OK : cuda_fail(h, e, "insert launch");
@@ -396,10 +405,16 @@ int build_graph(ns_handle* h, int batches) {
   if (h->graph_exec && h->graph_batches == batches) return NS_OK;
   if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
   cudaGraph_t g;
-  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e;
+  while ((int)h->walk_events.size() < 2 * batches) {
+    cudaEvent_t ev;
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(h, e, "event create");
+    h->walk_events.push_back(ev);
+  }
+  e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
   for (int b = 0; b < batches; ++b) {
-    int r = enqueue_batch(h);
+    int r = enqueue_batch(h, b);
     if (r) { cudaStreamEndCapture(h->stream, &g); return r; }
   }
   e = cudaStreamEndCapture(h->stream, &g);
@@ -453,6 +468,7 @@ int nested_init(ns_handle* h) {
         (r = alloc(h, (void**)&S.w_na, sizeof(int32_t) * k, "w_na")) ||
         (r = alloc(h, (void**)&S.w_nl, sizeof(int32_t) * k, "w_nl")) ||
         (r = alloc(h, (void**)&S.slot, sizeof(int32_t) * k, "slot")) ||
+        (r = alloc(h, (void**)&S.w_nb, sizeof(int64_t) * k, "w_nb")) ||
         (r = alloc(h, (void**)&S.dead_u, sizeof(double) * S.dead_cap * D, "dead_u")) ||
         (r = alloc(h, (void**)&S.dead_lnl, sizeof(double) * S.dead_cap, "dead_lnl")) ||
         (r = alloc(h, (void**)&S.dead_logw, sizeof(double) * S.dead_cap, "dead_logw")) ||
@@ -461,7 +477,7 @@ int nested_init(ns_handle* h) {
     WalkTask& T = tasks[e];
     std::memset(&T, 0, sizeof(T));
     T.surv = S.surv_u; T.u0 = S.w_u0; T.lnl0 = S.w_lnl0; T.u_out = S.w_uo; T.lnl_out = S.w_lo;
-    T.n_acc = S.w_na; T.n_like = S.w_nl;
+    T.n_acc = S.w_na; T.n_like = S.w_nl; T.n_bins = S.w_nb;
     T.lnl_star = -INFINITY; T.iteration = 0; T.walker_offset = 0;
     T.key0 = S.key0; T.key1 = S.key1; T.n_s = S.n_live - S.k; T.n = S.k; T.n_steps = S.n_steps;
     T.done = 0; T.event = e;
@@ -498,10 +514,12 @@ int nested_init(ns_handle* h) {
 
 void nested_free(ns_handle* h) {
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  for (cudaEvent_t ev : h->walk_events) cudaEventDestroy(ev);
+  h->walk_events.clear();
   for (auto& E : h->events) {
     NsState& S = E.ns;
     void* ptrs[] = {S.live_u, S.live_lnl, S.surv_u, S.w_u0, S.w_lnl0, S.w_uo, S.w_lo, S.w_na, S.w_nl,
-                    S.slot, S.dead_u, S.dead_lnl, S.dead_logw, S.dead_nlive};
+                    S.slot, S.w_nb, S.dead_u, S.dead_lnl, S.dead_logw, S.dead_nlive};
     for (void* p : ptrs) cudaFree(p);
     std::memset(&S, 0, sizeof(S));
   }
@@ -525,6 +543,9 @@ static void fill_progress(ns_handle* h, ns_progress* p) {
     p[e].mean_accept = S.mean_accept;
     p[e].n_steps = S.n_steps;
     p[e].done = S.done;
+    p[e].n_bins = S.n_bins_eval;
+    p[e].walk_ms = h->walk_ms;
+    p[e].kernel_launches = h->kernel_launches;
   }
 }
 
@@ -532,6 +553,7 @@ extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
   if (!h) return set_error(nullptr, NS_EINVAL, "handle is NULL");
   if (max_batches < 0) return set_error(h, NS_EINVAL, "max_batches < 0");
   cudaSetDevice(h->device);
+  cudaGetLastError();   // a stale error of an earlier call must not be reported here
   int r;
   bool all_done = true;
   for (auto& S : h->host_ns) all_done = all_done && S.done;
@@ -544,6 +566,13 @@ extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
     cudaError_t e = cudaGraphLaunch(h->graph_exec, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
     if ((r = download_states(h))) return r;
+    for (int i = 0; i < b; ++i) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, h->walk_events[2 * i], h->walk_events[2 * i + 1]);
+      if (e != cudaSuccess) return cuda_fail(h, e, "walk timing");
+      h->walk_ms += ms;
+    }
+    h->kernel_launches += 3 * (int64_t)b;
     left -= b;
     all_done = true;
     for (auto& S : h->host_ns) all_done = all_done && S.done;

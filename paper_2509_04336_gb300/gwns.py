@@ -53,7 +53,8 @@ class ns_event(C.Structure):
 class ns_progress(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("n_like", C.c_int64), ("log_z", C.c_double), ("dlogz", C.c_double),
                 ("log_x", C.c_double), ("lnl_star", C.c_double), ("mean_accept", C.c_double),
-                ("n_steps", C.c_int32), ("done", C.c_int32)]
+                ("n_steps", C.c_int32), ("done", C.c_int32), ("n_bins", C.c_int64), ("walk_ms", C.c_double),
+                ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

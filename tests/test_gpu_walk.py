@@ -121,3 +121,20 @@ def test_batches_match_oracle_fp64():
     assert p["n_steps"] == nested.retune(ref.stats[-1][1], ref.stats[-1][2], w.naccept,
                                          nested.batch_delay(w.naccept - 1, w.num_delete), w.maxmcmc)
     assert abs(lz - ref.log_z) < 1e-9
+
+
+def test_handles_in_sequence_and_step_statistics():
+    # A second handle after a first one has run graph-replayed batches and been freed.
+    w, ev = event("four_param_2det_taylorf2")
+    pri = priors(w, ev)
+    for rep in range(2):
+        cfg = gwns.make_config(w, pri, precision=synth.PREC_MIXED, max_iter=2)
+        h = gwns.ns_init([cfg], [ev])
+        try:
+            code, prog = gwns.ns_step(h, 2)
+            p = prog[0]
+            assert p["iterations"] == 2 and p["kernel_launches"] == 6
+            assert p["walk_ms"] > 0 and p["n_bins"] > 0
+            assert p["n_bins"] <= (p["n_like"] - w.n_live) * ev.n_bins
+        finally:
+            gwns.ns_free(h)
