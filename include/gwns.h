@@ -176,6 +176,23 @@ int ns_walk_batch(ns_handle* h, int event, const double* live_u, int n_live_pts,
                   double* u_out, double* lnl_out, int32_t* n_accept, int32_t* n_like,
                   int ptr_kind, void* stream);
 
+/* ns_walk_batch for callers that cannot allocate device memory after start-up (no
+ * counterpart in the paper).  Processes that reserve a fixed device-memory budget at
+ * start-up, or latency-critical loops that cannot absorb the device synchronisation of
+ * cudaMalloc/cudaFree, need a walk that allocates nothing: this call keeps the walk's task
+ * descriptor and block map in a fixed static device array (about 64 KB per GPU, held until
+ * the process exits) instead of growing scratch with cudaMalloc, and calls no allocation
+ * routine.  All arrays are DEVICE pointers with ns_walk_batch's layouts; the work is
+ * enqueued on `stream` and the call returns without waiting.  At most 8192 walkers per
+ * call (NS_EINVAL beyond).  The first call on a device looks up the array's address; make
+ * it before any stream capture.  Calls whose kernels overlap on the GPU share the array and
+ * race: order them on one stream.  Results equal ns_walk_batch's for the same arguments. */
+int ns_walk_batch_noalloc(ns_handle* h, int event, const double* live_u, int n_live_pts,
+                          const double* u0, const double* lnl0, double lnl_star,
+                          int n, int n_steps, int64_t iteration, int64_t walker_offset,
+                          double* u_out, double* lnl_out, int32_t* n_accept, int32_t* n_like,
+                          void* stream);
+
 /* Run up to max_batches batches of the sampler on every unfinished event (Sec. 2.2.3,
  * Sec. 3.2): deletion, evidence update, walk, insertion, walk-length retune and the
  * termination test all run on the device.  progress is [n_events] (may be NULL).

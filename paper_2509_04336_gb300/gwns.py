@@ -61,7 +61,7 @@ class ns_progress(C.Structure):
 
 
 EXPORTS = ("ns_init", "ns_waveform", "ns_likelihood_batch", "ns_walk_batch", "ns_step", "ns_evidence",
-           "ns_posterior", "ns_state_save", "ns_state_load", "ns_free", "ns_last_error")
+           "ns_posterior", "ns_state_save", "ns_state_load", "ns_walk_batch_noalloc", "ns_free", "ns_last_error")
 
 _lib = None
 
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
     lib.ns_posterior.argtypes = [P, I, P, P, C.c_int64, C.POINTER(C.c_int64)]
     lib.ns_state_save.argtypes = [P, C.c_char_p]
     lib.ns_state_load.argtypes = [P, C.c_char_p]
+    lib.ns_walk_batch_noalloc.argtypes = [P, I, P, I, P, P, D, I, I, C.c_int64, C.c_int64, P, P, P, P, V]
     lib.ns_free.argtypes = [P]
     lib.ns_free.restype = None
     lib.ns_last_error.argtypes = [P]
@@ -207,6 +208,19 @@ def ns_walk_batch(h, event: int, live_u, u0, lnl0, lnl_star: float, n_steps: int
                               u0.shape[0], n_steps, iteration, walker_offset, ps[3][0], ps[4][0], ps[5][0],
                               ps[6][0], kind, st)
     return _check(code, h, allow_warning=True)
+
+
+def ns_walk_batch_noalloc(h, event: int, live_u, u0, lnl0, lnl_star: float, n_steps: int, iteration: int,
+                          walker_offset: int, u_out, lnl_out, n_accept, n_like):
+    """The walk of ns_walk_batch without any device allocation; CUDA tensors only, enqueued
+    on the current torch stream."""
+    ps = _same_kind(live_u, u0, lnl0, u_out, lnl_out, n_accept, n_like)
+    if ps[0][1] != NS_PTR_DEVICE:
+        raise ValueError("ns_walk_batch_noalloc takes device (CUDA) tensors only")
+    code = _lib.ns_walk_batch_noalloc(h, event, ps[0][0], live_u.shape[0], ps[1][0], ps[2][0], float(lnl_star),
+                                      u0.shape[0], n_steps, iteration, walker_offset, ps[3][0], ps[4][0],
+                                      ps[5][0], ps[6][0], ps[0][2])
+    return _check(code, h)
 
 
 def ns_step(h, max_batches: int, n_events: int = 1):
