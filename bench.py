@@ -35,11 +35,12 @@ from paper_2509_04336_gb300 import synth  # noqa: E402
 WORKLOAD = "bbh11_3det_4s_taylorf2"
 METRIC = "wall-time to logZ (|Δ|≤0.1 vs FP64 oracle); lnL evals/s vs plain FP64 walk"
 UNIT = "lnL evals/s"
-# Algorithmic FP64 flops per active (walker, bin) of the mixed walk: phase over the
-# 8-function basis (8 FMA) and, per detector, the time-shift FMA and the reduction
-# subtract: 16 + 3 * 3 = 25.
-FP64_FLOPS_PER_WALKER_BIN = 25.0
-FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (152 SMs x 2.07 GHz x 4 flop/clk)
+# Algorithmic FP32 flops per evaluated (walker, bin) of the float-float walk (FMA = 2):
+# phase over the 8-function basis as float-float (per term 1 mul + 3 FMA + 7 add = 14),
+# its reduction (2); per detector the exact time-shift reduction (9), sincospi (20, its
+# polynomial), the complex multiply-accumulate (6) and two Kahan updates (8): 114 + 3 * 43.
+FP32_FLOPS_PER_WALKER_BIN = 243.0
+FP32_PEAK_TFLOPS = 80.5      # nominal GB300 FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz
 
 
 def rank_info():
@@ -254,13 +255,15 @@ def run_ours(args):
             p1 = p[0]
             res = {"ms": ms, "wall_s": wall, "evals": p1["n_like"] - p0[0]["n_like"],
                    "bins": p1["n_bins"] - p0[0]["n_bins"], "walk_ms": p1["walk_ms"] - p0[0]["walk_ms"],
+                   "spec": p1["n_spec"] - p0[0]["n_spec"],
                    "launches": p1["kernel_launches"] - p0[0]["kernel_launches"], "progress": p1,
                    "clocks": clocks.summary() if clocks else None}
             return res
         finally:
             gwns.ns_free(h)
 
-    mixed = timed_steps(synth.PREC_MIXED, args.steps, args.warmup, sample_clocks=True)
+    mixed = timed_steps(synth.PREC_MIXED_FF, args.steps, args.warmup, sample_clocks=True)
+    mixed64 = timed_steps(synth.PREC_MIXED, args.steps, args.warmup)
     plain = timed_steps(synth.PREC_FP64, args.steps, args.warmup)
 
     t_max = reduce(mixed["ms"], dist.ReduceOp.MAX if dist else None)
@@ -269,10 +272,12 @@ def run_ours(args):
     t_plain = reduce(plain["ms"], dist.ReduceOp.MAX if dist else None)
     evals_plain = reduce(float(plain["evals"]), dist.ReduceOp.SUM if dist else None)
     value_plain = evals_plain / (t_plain * 1e-3)
+    t_m64 = reduce(mixed64["ms"], dist.ReduceOp.MAX if dist else None)
+    value_m64 = reduce(float(mixed64["evals"]), dist.ReduceOp.SUM if dist else None) / (t_m64 * 1e-3)
 
     # end to end through the public API with host buffers: init (host data upload and the
     # initial live points), K batches, evidence read back
-    cfg = gwns.make_config(w, pri, precision=synth.PREC_MIXED)
+    cfg = gwns.make_config(w, pri, precision=synth.PREC_MIXED_FF)
     keep_ev = gwns.make_event(ev)
     torch.cuda.synchronize()
     barrier()
@@ -299,10 +304,12 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel (the walk): algorithmic FP64 flops / event-timed duration
+    # roofline of the dominant kernel (the walk): algorithmic FP32 flops of every evaluated
+    # (walker, bin) -- speculative evaluations included -- over its event-timed duration
     walk_launches = args.steps
     walk_ms_avg = mixed["walk_ms"] / walk_launches
-    achieved = mixed["bins"] * FP64_FLOPS_PER_WALKER_BIN / (mixed["walk_ms"] * 1e-3) / 1e12
+    bins_evaluated = mixed["bins"] * mixed["spec"] / max(mixed["evals"], 1)
+    achieved = bins_evaluated * FP32_FLOPS_PER_WALKER_BIN / (mixed["walk_ms"] * 1e-3) / 1e12
     cpu_rate, cpu_info = oracle_walk_rate(w, ev, budget_s=args.cpu_seconds)
     clocks = mixed["clocks"] or {}
     line = {
@@ -311,21 +318,25 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: 3 detectors, 4017 bins (4 s, 20-1024 Hz), TaylorF2, 11 params, "
                                f"n_live 1000, num_delete 500, naccept 60, SNR 39.6, seeded noise",
-                   "precision": "mixed (FP32 sums, FP64 phase)", "step": "one sampler batch (select, walk, insert)",
+                   "precision": "mixed: FP32 sums, float-float phase, FP64 per-walker constants and lnL assembly",
+                   "step": "one sampler batch (select, walk, insert)",
                    "l2": "flushed (256 MB write) between timed steps", "events_per_rank": 1},
         "plain_fp64": {"value": value_plain, "unit": UNIT, "ms_per_step": t_plain / args.steps},
+        "mixed_fp64_phase": {"value": value_m64, "unit": UNIT, "ms_per_step": t_m64 / args.steps},
         "mixed_over_plain": value / value_plain,
+        "speculative_evals_per_eval": mixed["spec"] / max(mixed["evals"], 1),
+        "spec_depth": mixed["progress"]["spec_depth"],
         "mean_walk_steps": mixed["progress"]["n_steps"], "mean_accept": mixed["progress"]["mean_accept"],
         "active_bins_per_eval": mixed["bins"] / max(mixed["evals"], 1),
         "e2e": {"value": e2e_evals / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": args.steps, "log_z": lz, "log_z_err": lz_err},
         "gpu_launches": int(mixed["launches"]),
-        "roofline": {"bound": "alu", "pipe": "fp64", "kernel": "walk_kernel<mixed,3>",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+        "roofline": {"bound": "alu", "pipe": "fp32", "kernel": "walk_kernel<2,3> (float-float phase)",
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "avg_launch_ms": walk_ms_avg,
-                     "peak_source": "nominal GB300 FP64, 152 SMs x 2.07 GHz x 4 flop/clk (recipe); "
-                                    "FMA microbenchmark measured 1.196"},
+                     "peak_source": "nominal GB300 FP32, 152 SMs x 128 lanes x 2 flop x 2.07 GHz; "
+                                    "FMA microbenchmark measured 74.7"},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": cpu_info["sample"]},
         "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
@@ -337,6 +348,25 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """A small case for profilers: N batches of the bench workload, no timing."""
+    from paper_2509_04336_gb300 import build, gwns
+    import torch
+    build.build()
+    gwns.load()
+    torch.cuda.set_device(0)
+    w, ev = library_event(synth.workload(WORKLOAD), 0, 0)
+    pri = synth.priors_with_injection(w, ev)
+    h = gwns.ns_init([gwns.make_config(w, pri, precision=args.precision)], [ev])
+    try:
+        for _ in range(args.profile_batches):
+            _, p = gwns.ns_step(h, 1)
+        print(json.dumps(p[0]))
+    finally:
+        gwns.ns_free(h)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,7 +374,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-batches", type=int, default=0,
+                    help="run this many batches of the workload without timing (a small case for ncu)")
+    ap.add_argument("--precision", type=int, default=synth.PREC_MIXED_FF)
     args = ap.parse_args()
+    if args.profile_batches > 0:
+        return run_profile_case(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -68,9 +68,13 @@ extern "C" {
 #define NS_WAVEFORM_TAYLORF2 0      /* 3.5PN aligned-spin TaylorF2, zero above f_ISCO  */
 #define NS_WAVEFORM_PHENOMD_FORM 1  /* IMRPhenomD-form inspiral-merger-ringdown        */
 
-#define NS_PREC_FP64 0   /* every step in FP64 (the plain walk)                              */
-#define NS_PREC_MIXED 1  /* FP32 amplitude and inner products with compensated sums;           */
-                         /* FP64-accurate phase and its reduction; FP64 lnL assembly, evidence */
+#define NS_PREC_FP64 0      /* every step in FP64 (the plain walk)                              */
+#define NS_PREC_MIXED 1     /* FP32 amplitude and inner products with compensated sums; the     */
+                            /* phase, its reduction and the time shift in FP64; FP64 lnL         */
+                            /* assembly and evidence                                             */
+#define NS_PREC_MIXED_FF 2  /* as NS_PREC_MIXED, but the phase is carried as a float-float pair  */
+                            /* (about 48-bit significand) on the FP32 pipe and the time shift is */
+                            /* reduced exactly through a 9-bit head; per-walker constants FP64   */
 
 #define NS_TERM_DLOGZ 0           /* stop when ln(Z + L_max X) - ln Z < term_value (Sec. 4.1.1)   */
 #define NS_TERM_FRAC_REMAINING 1  /* stop when L_mean X < term_value * Z (Sec. 4.2)              */
@@ -104,6 +108,9 @@ typedef struct ns_config {
     int32_t max_iter;     /* hard cap on batches (0: 1000000)                       */
     int32_t n_steps0;     /* first walk length (0: ceil(naccept / 0.25))            */
     uint64_t seed;        /* Philox key word 0; key word 1 is the event index      */
+    int32_t spec_depth;   /* walk steps evaluated per round (1..32); 0: chosen per batch
+                             from the acceptance rate.  Any value gives the same chain.  */
+    int32_t reserved;     /* must be 0                                              */
 } ns_config;
 
 /* One detector's data.  Pointers are HOST arrays of n_bins doubles, copied by ns_init. */
@@ -141,6 +148,10 @@ typedef struct ns_progress {
     double walk_ms;       /* device time of this handle's walk launches so far [ms], */
                           /* from CUDA events on the launching stream (all events)  */
     int64_t kernel_launches; /* kernels launched by ns_step so far (all events)     */
+    int64_t n_spec;       /* likelihoods evaluated by walks so far, including those   */
+                          /* evaluated ahead and dropped after an earlier acceptance  */
+    int32_t spec_depth;   /* speculation depth of the next batch                    */
+    int32_t reserved;
 } ns_progress;
 
 typedef struct ns_handle ns_handle;

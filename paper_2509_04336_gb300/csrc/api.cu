@@ -72,7 +72,9 @@ static int check_config(const ns_config& c, int e) {
   if (c.num_delete < 1 || c.n_live - c.num_delete < 2)
     return set_error(nullptr, NS_EINVAL, "event %d: need 1 <= num_delete <= n_live - 2", e);
   if (c.naccept < 1 || c.maxmcmc < 1) return set_error(nullptr, NS_EINVAL, "event %d: naccept, maxmcmc >= 1", e);
-  if (c.precision != NS_PREC_FP64 && c.precision != NS_PREC_MIXED)
+  if (c.spec_depth < 0 || c.spec_depth > kSpecMax || c.reserved != 0)
+    return set_error(nullptr, NS_EINVAL, "event %d: spec_depth must be in 0..%d (reserved 0)", e, kSpecMax);
+  if (c.precision != NS_PREC_FP64 && c.precision != NS_PREC_MIXED && c.precision != NS_PREC_MIXED_FF)
     return set_error(nullptr, NS_EINVAL, "event %d: unknown precision %d", e, c.precision);
   if (c.waveform != NS_WAVEFORM_TAYLORF2 && c.waveform != NS_WAVEFORM_PHENOMD_FORM)
     return set_error(nullptr, NS_EINVAL, "event %d: unknown waveform %d", e, c.waveform);
@@ -111,6 +113,7 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
   E.n_bins = in.n_bins;
   const int nb = in.n_bins, nd = in.n_det;
   std::vector<double> basis((size_t)nb * kBasis);
+  std::vector<float2> basis_ff((size_t)nb * kBasis);
   std::vector<double2> z64((size_t)nd * nb);
   std::vector<float2> z32((size_t)nd * nb);
   std::vector<double> pref((size_t)nd * nb);
@@ -127,6 +130,10 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
     g[5] = c3 * c3;               // f^2/3
     g[6] = lf;                    // ln f
     g[7] = c3 * lf;               // f^1/3 ln f
+    for (int j = 0; j < kBasis; ++j) {
+      float hi = (float)g[j];
+      basis_ff[(size_t)k * kBasis + j] = make_float2(hi, (float)(g[j] - (double)hi));
+    }
   }
   for (int d = 0; d < nd; ++d) {
     const ns_detector& det = in.det[d];
@@ -152,11 +159,13 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
   // device copies
   cudaError_t err;
   if ((err = cudaMalloc(&E.d_basis64, basis.size() * sizeof(double))) != cudaSuccess ||
+      (err = cudaMalloc(&E.d_basis_ff, basis_ff.size() * sizeof(float2))) != cudaSuccess ||
       (err = cudaMalloc(&E.d_z64, z64.size() * sizeof(double2))) != cudaSuccess ||
       (err = cudaMalloc(&E.d_z32, z32.size() * sizeof(float2))) != cudaSuccess ||
       (err = cudaMalloc(&E.d_hh_prefix, pref.size() * sizeof(double))) != cudaSuccess)
     return set_error(nullptr, NS_ENOMEM, "event %d: device allocation failed: %s", e, cudaGetErrorString(err));
   if ((err = cudaMemcpy(E.d_basis64, basis.data(), basis.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(E.d_basis_ff, basis_ff.data(), basis_ff.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMemcpy(E.d_z64, z64.data(), z64.size() * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMemcpy(E.d_z32, z32.data(), z32.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMemcpy(E.d_hh_prefix, pref.data(), pref.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -176,6 +185,8 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
       D.vertex[d][i] = in.det[d].vertex[i];
       D.xarm[d][i] = in.det[d].x_arm[i];
       D.yarm[d][i] = in.det[d].y_arm[i];
+      D.xarm32[d][i] = (float)in.det[d].x_arm[i];
+      D.yarm32[d][i] = (float)in.det[d].y_arm[i];
     }
   int nd_dim = 0;
   for (int i = 0; i < kParams; ++i) {
@@ -204,6 +215,7 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
   }
   D.n_dim = nd_dim;
   D.basis64 = E.d_basis64;
+  D.basis_ff = E.d_basis_ff;
   D.z64 = E.d_z64;
   D.z32 = E.d_z32;
   D.hh_prefix = E.d_hh_prefix;
@@ -213,10 +225,12 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
 
 void free_event(EventHost& E) {
   cudaFree(E.d_basis64);
+  cudaFree(E.d_basis_ff);
   cudaFree(E.d_z64);
   cudaFree(E.d_z32);
   cudaFree(E.d_hh_prefix);
   E.d_basis64 = nullptr;
+  E.d_basis_ff = nullptr;
   E.d_z64 = nullptr;
   E.d_z32 = nullptr;
   E.d_hh_prefix = nullptr;
@@ -278,6 +292,9 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
   *out = h;
   return NS_OK;
 }
+
+// Speculation depth of a stand-alone walk when the configuration leaves it automatic.
+int default_spec(int precision) { return precision == NS_PREC_FP64 ? 4 : 16; }
 
 static cudaStream_t pick_stream(ns_handle* h, void* stream) {
   return stream ? (cudaStream_t)stream : h->stream;
@@ -385,6 +402,7 @@ extern "C" int ns_walk_batch(ns_handle* h, int event, const double* live_u, int 
   T.n_steps = n_steps;
   T.done = 0;
   T.event = event;
+  T.spec = E.cfg.spec_depth > 0 ? E.cfg.spec_depth : default_spec(h->precision);
   cudaError_t e;
   // block -> (event, walker) maps, one task slot of the handle
   int r = ensure_scratch(h, h->scratch_map, sizeof(int32_t) * 2 * (size_t)n + sizeof(WalkTask));

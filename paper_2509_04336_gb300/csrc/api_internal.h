@@ -21,12 +21,14 @@ struct Scratch {
 // it in place, so a captured graph replays batches without host round trips.
 struct NsState {
   double log_x, log_z, lnl_star, dlogz, mean_accept, lnl_max, delay_k, term_value;
-  int64_t n_dead, n_like, iteration, max_iter, dead_cap, n_bins_eval;
+  int64_t n_dead, n_like, iteration, max_iter, dead_cap, n_bins_eval, n_spec_eval;
   int32_t n_live, k, D, n_steps, naccept, maxmcmc, term_kind, done, zero_accept, overflow;
+  int32_t spec, spec_auto, spec_cap, pad;
   uint64_t key0, key1;
   double* live_u;      // [n_live][D]
   double* live_lnl;    // [n_live]
   double* surv_u;      // [n_live - k][D]
+  float* surv32;       // [n_live - k][D] FP32 copy for the walk's candidate screen
   double* w_u0;        // [k][D]
   double* w_lnl0;      // [k]
   double* w_uo;        // [k][D]
@@ -35,6 +37,7 @@ struct NsState {
   int32_t* w_nl;       // [k]
   int32_t* slot;       // [k]
   int64_t* w_nb;       // [k] active bins evaluated per walker
+  int64_t* w_ns;       // [k] likelihoods evaluated per walker, speculative ones included
   double* dead_u;      // [dead_cap][D]
   double* dead_lnl;    // [dead_cap]
   double* dead_logw;   // [dead_cap]
@@ -46,6 +49,7 @@ struct EventHost {
   int n_det = 0, n_bins = 0, n_dim = 0;
   EventDev dev;
   double* d_basis64 = nullptr;
+  float2* d_basis_ff = nullptr;
   double2* d_z64 = nullptr;
   float2* d_z32 = nullptr;
   double* d_hh_prefix = nullptr;
@@ -83,4 +87,5 @@ int set_error(ns_handle* h, int code, const char* fmt, ...);
 int cuda_fail(ns_handle* h, cudaError_t e, const char* what);
 int ensure_scratch(ns_handle* h, gwns::Scratch& s, size_t bytes);
 int nested_init(ns_handle* h);
+int default_spec(int precision);
 void nested_free(ns_handle* h);

@@ -15,6 +15,7 @@ constexpr int kThreads = 128;   // threads per walker CTA
 // replays without host involvement.
 struct WalkTask {
   const double* surv;      // [n_s][D] survivors
+  const float* surv32;     // [n_s][D] FP32 copy used only to screen candidates (may be null)
   const double* u0;        // [n][D] starts
   const double* lnl0;      // [n]
   double* u_out;           // [n][D]
@@ -22,6 +23,7 @@ struct WalkTask {
   int32_t* n_acc;          // [n]
   int32_t* n_like;         // [n]
   int64_t* n_bins;         // [n] active bins evaluated per walker (may be null)
+  int64_t* n_spec;         // [n] likelihoods evaluated speculatively, used or not (may be null)
   double lnl_star;
   int64_t iteration;
   int64_t walker_offset;
@@ -31,8 +33,10 @@ struct WalkTask {
   int32_t n_steps;
   int32_t done;
   int32_t event;           // index into the event table
-  int32_t pad;
+  int32_t spec;            // proposals evaluated per round (1 .. kSpecMax)
 };
+
+constexpr int kSpecMax = 32;   // speculation depth limit (one warp of proposals)
 
 // Launch wrappers (kernels.cu).  Every wrapper returns the launch error.
 cudaError_t launch_likelihood(int precision, int n_det, const EventDev* d_ev, const double* d_theta,

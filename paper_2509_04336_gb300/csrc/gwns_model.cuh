@@ -56,15 +56,18 @@ struct EventDev {
   double f_min, df, gmst;
   double dd_total;                     // sum_det <d|d>
   double vertex[kMaxDet][3], xarm[kMaxDet][3], yarm[kMaxDet][3];
+  float xarm32[kMaxDet][3], yarm32[kMaxDet][3];
   PriorDev prior[kParams];
   int dim_param[kMaxDim];              // physical index of each sampled dimension
   const double* basis64;               // [n_bins][kBasis]
+  const float2* basis_ff;              // [n_bins][kBasis] (hi, lo) float-float copy of basis64
   const double2* z64;                  // [n_det][n_bins]
   const float2* z32;                   // [n_det][n_bins]
   const double* hh_prefix;             // [n_det][n_bins] inclusive prefix sums of 4 df f^-7/3 / S
 };
 
-// Per-walker constants of one likelihood evaluation.
+// Per-walker constants of one likelihood evaluation.  The float fields are the
+// float-float split used by the FP32-pipe phase path (make_ff).
 struct WalkerParams {
   double C[kBasis];
   double phase0;
@@ -73,6 +76,10 @@ struct WalkerParams {
   double hh;
   int k_end;
   int pad;
+  float Ch[kBasis], Cl[kBasis];        // C_j = Ch + Cl
+  float ph0h, ph0l;                    // phase0 = ph0h + ph0l
+  float sa[kMaxDet];                   // frac(tau f_min)                       [cycles]
+  float sbh[kMaxDet], sbl[kMaxDet];    // tau df = sbh + sbl, sbh with 9 significant bits
 };
 
 // ---------------------------------------------------------------- Philox4x64-10
@@ -176,7 +183,8 @@ __device__ inline void taylorf2_pn_coeffs(double eta, double delta, double chis,
 // Number of bins with f_k <= f_cut (f_k = f_min + k df, exactly as the grid is defined).
 __device__ inline int bins_below(double f_min, double df, int n_bins, double f_cut) {
   if (!(f_cut >= f_min)) return 0;
-  double x = floor((f_cut - f_min) / df);
+  // a first guess from the reciprocal; the two loops make the count exact
+  double x = floor((f_cut - f_min) * (1.0 / df));
   long k = (long)fmin(x, (double)n_bins);
   while (k + 1 <= n_bins - 1 && f_min + df * (double)(k + 1) <= f_cut) ++k;
   while (k >= 0 && (k > n_bins - 1 || f_min + df * (double)k > f_cut)) --k;
@@ -255,6 +263,169 @@ __device__ inline void taylorf2_setup(const EventDev& ev, const double* th, doub
   p.hh = hh;
 }
 
+// Float-float split of the per-walker constants.  k * sbh is exact in FP32 for k < 2^15
+// because sbh keeps 9 significant bits, so the time-shift phase k tau df is reduced exactly.
+__device__ inline void make_ff(const EventDev& ev, WalkerParams& p) {
+  for (int j = 0; j < kBasis; ++j) {
+    float h = (float)p.C[j];
+    p.Ch[j] = h;
+    p.Cl[j] = (float)(p.C[j] - (double)h);
+  }
+  float h0 = (float)p.phase0;
+  p.ph0h = h0;
+  p.ph0l = (float)(p.phase0 - (double)h0);
+  for (int det = 0; det < ev.n_det; ++det) {
+    double a = p.tau[det] * ev.f_min;
+    p.sa[det] = (float)(a - rint(a));
+    double b = p.tau[det] * ev.df;
+    float bh = __int_as_float(__float_as_int((float)b) & (int)0xFFFF8000u);
+    p.sbh[det] = bh;
+    p.sbl[det] = (float)(b - (double)bh);
+  }
+}
+
+// ---------------------------------------------------------------- lean setup (mixed paths)
+// The mixed paths need FP64 only for what moves the phase: chirp mass, mass ratio, spins,
+// coalescence phase and time, and the arrival delays.  Amplitude, inclination, polarisation
+// and the antenna patterns only scale h and are computed in FP32.  Roots are FP32 seeds with
+// two FP64 Newton steps each (quadratic convergence from ~1e-7 to below 1 ulp), which keeps
+// the FP64 instruction count and latency of a proposal low.
+
+// a^(-1/3) for a > 0: w <- w (4 - a w^3) / 3.
+__device__ __forceinline__ double rcbrt_newton(double a) {
+  double w = (double)rcbrtf((float)a);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    double w3 = w * w * w;
+    w = w * (4.0 - a * w3) * (1.0 / 3.0);
+  }
+  return w;
+}
+
+// a^(-1/5) for a > 0: z <- z (6 - a z^5) / 5.
+__device__ __forceinline__ double rfifth_newton(double a) {
+  double z = (double)__powf((float)a, -0.2f);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    double z2 = z * z;
+    double z5 = z2 * z2 * z;
+    z = z * (6.0 - a * z5) * 0.2;
+  }
+  return z;
+}
+
+// The sampled physical quantities a mixed-precision likelihood needs, from unit-cube u.
+struct LeanTheta {
+  double mc, q, chi1, chi2, phic, tc, ra, sdec, cdec;
+  float dl, ci, psi;
+};
+
+__device__ inline void unit_to_lean(const EventDev& ev, const double* u, LeanTheta& t) {
+  int d = 0;
+  double x[kParams];
+  double ci = 0.0, sd = 0.0, cd = 1.0;
+  bool have_ci = false, have_dec = false;
+  for (int i = 0; i < kParams; ++i) {
+    const PriorDev& p = ev.prior[i];
+    if (p.kind == kFixed) {
+      x[i] = p.value;
+      if (i == 5) { ci = p.cosv; have_ci = true; }
+      if (i == 10) { sd = p.sinv; cd = p.cosv; have_dec = true; }
+      continue;
+    }
+    double v = u[d++];
+    if (p.kind == kUniform) {
+      x[i] = __dadd_rn(p.lo, __dmul_rn(v, p.w));
+    } else if (p.kind == kPowerLaw) {
+      double y = __dadd_rn(p.A, __dmul_rn(v, p.B));
+      x[i] = (double)powf((float)y, (float)(1.0 / p.e));   // amplitude-only parameter (distance)
+    } else if (p.kind == kSine) {
+      double c = fmin(1.0, fmax(-1.0, __dsub_rn(p.A, __dmul_rn(v, p.B))));
+      x[i] = 0.0;
+      if (i == 5) { ci = c; have_ci = true; } else x[i] = acos(c);
+    } else {
+      double sv = fmin(1.0, fmax(-1.0, __dadd_rn(p.A, __dmul_rn(v, p.B))));
+      x[i] = 0.0;
+      if (i == 10) { sd = sv; cd = sqrt(fmax(0.0, (1.0 - sv) * (1.0 + sv))); have_dec = true; }
+      else x[i] = asin(sv);
+    }
+  }
+  if (!have_ci) ci = cos(x[5]);
+  if (!have_dec) sincos(x[10], &sd, &cd);
+  t.mc = x[0]; t.q = x[1]; t.chi1 = x[2]; t.chi2 = x[3];
+  t.dl = (float)x[4]; t.ci = (float)ci; t.psi = (float)x[6];
+  t.phic = x[7]; t.tc = x[8]; t.ra = x[9]; t.sdec = sd; t.cdec = cd;
+}
+
+__device__ inline void taylorf2_setup_lean(const EventDev& ev, const LeanTheta& t, WalkerParams& p) {
+  const double q = t.q;
+  const double opq = 1.0 + q;
+  const double r_opq = 1.0 / opq;
+  const double eta = q * r_opq * r_opq;
+  const double delta = (1.0 - q) * r_opq;
+  const double chis = 0.5 * (t.chi1 + t.chi2), chia = 0.5 * (t.chi1 - t.chi2);
+  const double pmc = kPi * kMsunS * t.mc;           // pi Mc [s]
+  const double w = rcbrt_newton(pmc);                // (pi Mc)^(-1/3)
+  const double z = rfifth_newton(eta);               // eta^(-1/5)
+  const double c1 = pmc * w * w * z;                 // (pi M)^(1/3) = (pi Mc)^(1/3) eta^(-1/5)
+  const double z2 = z * z;
+  const double ci1 = w * eta * z2 * z2;              // (pi M)^(-1/3)
+  const double ci1_3 = ci1 * ci1 * ci1;                 // 1/(pi M)
+  p.k_end = bins_below(ev.f_min, ev.df, ev.n_bins, (1.0 / kSix15) * ci1_3);
+  double a[8], al[8];
+  taylorf2_pn_coeffs(eta, delta, chis, chia, a, al);
+  const double lpm = 3.0 * log(c1);
+  const double ci2 = ci1 * ci1, ci3 = ci1_3, ci5 = ci3 * ci2;
+  const double pre = (3.0 / (256.0 * kPi)) * opq * opq / q;   // 3/(256 pi eta)
+  p.C[0] = pre * ci5 * a[0];
+  p.C[1] = pre * ci3 * a[2];
+  p.C[2] = pre * ci2 * a[3];
+  p.C[3] = pre * ci1 * a[4];
+  p.C[4] = pre * c1 * (a[6] + al[6] * lpm / 3.0);
+  p.C[5] = pre * c1 * c1 * a[7];
+  p.C[6] = pre * al[5] / 3.0;
+  p.C[7] = pre * c1 * al[6] / 3.0;
+  p.phase0 = pre * (a[5] + al[5] * lpm / 3.0) - t.phic / kPi - 0.125;
+  // sky direction in FP64 (it sets the arrival delays), the rest in FP32
+  double sp, cp;
+  sincos(t.ra - ev.gmst, &sp, &cp);
+  const double n0 = t.cdec * cp, n1 = t.cdec * sp, n2 = t.sdec;
+  const float spf = (float)sp, cpf = (float)cp, ctf = (float)t.sdec, stf = (float)t.cdec;
+  float ssf, csf;
+  sincosf(t.psi, &ssf, &csf);
+  const float X0 = spf * csf - ssf * cpf * ctf, X1 = -(cpf * csf + ssf * spf * ctf), X2 = ssf * stf;
+  const float Y0 = -spf * ssf - csf * cpf * ctf, Y1 = cpf * ssf - csf * spf * ctf, Y2 = stf * csf;
+  const float mcs = (float)(t.mc * kMsunS);
+  const float K = (float)kAmp0 * sqrtf(mcs) * cbrtf(mcs) * (float)(kC / kMpcM) / t.dl;
+  const float ap = 0.5f * (1.0f + t.ci * t.ci);
+  double hh = 0.0;
+  for (int det = 0; det < ev.n_det; ++det) {
+    const float* xa = ev.xarm32[det];
+    const float* ya = ev.yarm32[det];
+    float xX = xa[0] * X0 + xa[1] * X1 + xa[2] * X2, xY = xa[0] * Y0 + xa[1] * Y1 + xa[2] * Y2;
+    float yX = ya[0] * X0 + ya[1] * X1 + ya[2] * X2, yY = ya[0] * Y0 + ya[1] * Y1 + ya[2] * Y2;
+    float fp = 0.5f * (xX * xX - xY * xY - yX * yX + yY * yY);
+    float fc = xX * xY - yX * yY;
+    float pr = fp * ap, pi_ = -fc * t.ci;
+    p.kp_re[det] = (double)(K * pr);
+    p.kp_im[det] = (double)(K * pi_);
+    const double* r = ev.vertex[det];
+    p.tau[det] = t.tc - (r[0] * n0 + r[1] * n1 + r[2] * n2) * (1.0 / kC);
+    double psum = p.k_end > 0 ? ev.hh_prefix[(size_t)det * ev.n_bins + p.k_end - 1] : 0.0;
+    // K ~ 1e-21: its square underflows FP32, so |K P|^2 is formed in FP64
+    hh += (p.kp_re[det] * p.kp_re[det] + p.kp_im[det] * p.kp_im[det]) * psum;
+  }
+  p.hh = hh;
+}
+
+// Lean constants from a physical theta (ns_likelihood_batch in the mixed paths).
+__device__ inline void theta_to_lean(const double* th, LeanTheta& t) {
+  t.mc = th[0]; t.q = th[1]; t.chi1 = th[2]; t.chi2 = th[3];
+  t.dl = (float)th[4]; t.ci = (float)cos(th[5]); t.psi = (float)th[6];
+  t.phic = th[7]; t.tc = th[8]; t.ra = th[9];
+  sincos(th[10], &t.sdec, &t.cdec);
+}
+
 // ---------------------------------------------------------------- per-bin accumulation
 struct AccF64 {
   double re[kMaxDet], im[kMaxDet];
@@ -313,6 +484,43 @@ __device__ __forceinline__ void bin_accumulate_mixed(const EventDev& ev, const W
     float r = (float)(ph - rint(ph));
     float s, c;
     sincospif(2.0f * r, &s, &c);
+    float2 z = ev.z32[(size_t)det * ev.n_bins + k];
+    kahan_add(acc.re[det], acc.cre[det], fmaf(z.x, c, z.y * s));
+    kahan_add(acc.im[det], acc.cim[det], fmaf(z.y, c, -z.x * s));
+  }
+}
+
+// Float-float path: the phase sum_j C_j g_j is accumulated as an unevaluated (hi, lo) pair
+// with error-free products (FMA) and two-sums, reduced modulo one cycle exactly, and the
+// time shift k tau df is added through its 9-bit head; FP32 sincos and compensated sums.
+template <int NDET>
+__device__ __forceinline__ void bin_accumulate_ff(const EventDev& ev, const WalkerParams& p, int k,
+                                                  AccF32& acc) {
+  const float2* g = ev.basis_ff + (size_t)k * kBasis;
+  float sh = p.ph0h, sl = p.ph0l;
+#pragma unroll
+  for (int j = 0; j < kBasis; ++j) {
+    float2 gj = g[j];
+    float q = p.Ch[j] * gj.x;
+    float e = fmaf(p.Ch[j], gj.x, -q);
+    e = fmaf(p.Ch[j], gj.y, e);
+    e = fmaf(p.Cl[j], gj.x, e);
+    float t = sh + q;
+    float bb = t - sh;
+    float err = (sh - (t - bb)) + (q - bb);
+    sh = t;
+    sl += err + e;
+  }
+  const float r0 = (sh - rintf(sh)) + sl;
+  const float kf = (float)k;
+#pragma unroll
+  for (int det = 0; det < NDET; ++det) {
+    float kb = kf * p.sbh[det];
+    float x = kb - rintf(kb);
+    float ph = (r0 + p.sa[det]) + x + kf * p.sbl[det];
+    ph = ph - rintf(ph);
+    float s, c;
+    sincospif(2.0f * ph, &s, &c);
     float2 z = ev.z32[(size_t)det * ev.n_bins + k];
     kahan_add(acc.re[det], acc.cre[det], fmaf(z.x, c, z.y * s));
     kahan_add(acc.im[det], acc.cim[det], fmaf(z.y, c, -z.x * s));

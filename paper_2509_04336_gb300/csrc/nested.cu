@@ -169,7 +169,11 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(NsState* states, Wa
   const int ns = n - k;
   for (int i = tid; i < ns; i += kSelThreads) {
     int id = idx[k + i];
-    for (int d = 0; d < D; ++d) S.surv_u[(size_t)i * D + d] = S.live_u[(size_t)id * D + d];
+    for (int d = 0; d < D; ++d) {
+      double v = S.live_u[(size_t)id * D + d];
+      S.surv_u[(size_t)i * D + d] = v;
+      S.surv32[(size_t)i * D + d] = (float)v;
+    }
   }
   const uint64_t it = (uint64_t)S.iteration;
   for (int j = tid; j < k; j += kSelThreads) {
@@ -200,10 +204,11 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
   NsState& S = states[blockIdx.x];
   if (S.done) return;
   const int k = S.k, D = S.D, n = S.n_live, tid = threadIdx.x;
-  double acc = 0.0, calls = 0.0, zero = 0.0, bins = 0.0;
+  double acc = 0.0, calls = 0.0, zero = 0.0, bins = 0.0, spec = 0.0;
   for (int j = tid; j < k; j += kSelThreads) {
     int s = S.slot[j];
     bins += (double)S.w_nb[j];
+    spec += (double)S.w_ns[j];
     for (int d = 0; d < D; ++d) S.live_u[(size_t)s * D + d] = S.w_uo[(size_t)j * D + d];
     S.live_lnl[s] = S.w_lo[j];
     acc += (double)S.w_na[j];
@@ -214,6 +219,7 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
   const double tot_calls = block_sum(calls, buf);
   const double n_zero = block_sum(zero, buf);
   const double tot_bins = block_sum(bins, buf);
+  const double tot_spec = block_sum(spec, buf);
   __syncthreads();
   double mx = -INFINITY;
   for (int i = tid; i < n; i += kSelThreads) mx = fmax(mx, S.live_lnl[i]);
@@ -226,6 +232,15 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
     S.mean_accept = mean_acc;
     S.n_like += (int64_t)tot_calls;
     S.n_bins_eval += (int64_t)tot_bins;
+    S.n_spec_eval += (int64_t)tot_spec;
+    // speculation depth of the next batch: about 0.7 / p in-bounds proposals per round,
+    // p the acceptance per likelihood call of this batch, so that the first acceptance
+    // falls on average about halfway through a round
+    if (S.spec_auto) {
+      double p = mean_acc / fmax(tot_calls / (double)k, 1.0);
+      double m = p > 0.0 ? floor(0.7 / p + 0.5) : (double)S.spec_cap;
+      S.spec = (int32_t)fmin(fmax(m, 1.0), (double)S.spec_cap);
+    }
     if (n_zero > 0.0) S.zero_accept = 1;
     // walk-length retune (batch-scaled delay)
     double ns = (double)S.n_steps;
@@ -246,6 +261,7 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
     if (stop || S.iteration >= S.max_iter) S.done = 1;
     tasks[blockIdx.x].done = S.done;
     tasks[blockIdx.x].n_steps = S.n_steps;
+    tasks[blockIdx.x].spec = S.spec;
   }
 }
 
@@ -457,10 +473,14 @@ int nested_init(ns_handle* h) {
     S.key0 = c.seed;
     S.key1 = (uint64_t)e;
     S.dead_cap = (int64_t)S.k * 64;
+    S.spec_auto = c.spec_depth == 0;
+    S.spec_cap = h->precision == 0 ? 8 : kSpecMax;
+    S.spec = c.spec_depth > 0 ? c.spec_depth : 4;
     const size_t n = S.n_live, k = S.k, D = S.D;
     if ((r = alloc(h, (void**)&S.live_u, sizeof(double) * n * D, "live_u")) ||
         (r = alloc(h, (void**)&S.live_lnl, sizeof(double) * n, "live_lnl")) ||
         (r = alloc(h, (void**)&S.surv_u, sizeof(double) * (n - k) * D, "surv_u")) ||
+        (r = alloc(h, (void**)&S.surv32, sizeof(float) * (n - k) * D, "surv32")) ||
         (r = alloc(h, (void**)&S.w_u0, sizeof(double) * k * D, "w_u0")) ||
         (r = alloc(h, (void**)&S.w_lnl0, sizeof(double) * k, "w_lnl0")) ||
         (r = alloc(h, (void**)&S.w_uo, sizeof(double) * k * D, "w_uo")) ||
@@ -469,6 +489,7 @@ int nested_init(ns_handle* h) {
         (r = alloc(h, (void**)&S.w_nl, sizeof(int32_t) * k, "w_nl")) ||
         (r = alloc(h, (void**)&S.slot, sizeof(int32_t) * k, "slot")) ||
         (r = alloc(h, (void**)&S.w_nb, sizeof(int64_t) * k, "w_nb")) ||
+        (r = alloc(h, (void**)&S.w_ns, sizeof(int64_t) * k, "w_ns")) ||
         (r = alloc(h, (void**)&S.dead_u, sizeof(double) * S.dead_cap * D, "dead_u")) ||
         (r = alloc(h, (void**)&S.dead_lnl, sizeof(double) * S.dead_cap, "dead_lnl")) ||
         (r = alloc(h, (void**)&S.dead_logw, sizeof(double) * S.dead_cap, "dead_logw")) ||
@@ -476,8 +497,8 @@ int nested_init(ns_handle* h) {
       return r;
     WalkTask& T = tasks[e];
     std::memset(&T, 0, sizeof(T));
-    T.surv = S.surv_u; T.u0 = S.w_u0; T.lnl0 = S.w_lnl0; T.u_out = S.w_uo; T.lnl_out = S.w_lo;
-    T.n_acc = S.w_na; T.n_like = S.w_nl; T.n_bins = S.w_nb;
+    T.surv = S.surv_u; T.surv32 = S.surv32; T.u0 = S.w_u0; T.lnl0 = S.w_lnl0; T.u_out = S.w_uo; T.lnl_out = S.w_lo;
+    T.n_acc = S.w_na; T.n_like = S.w_nl; T.n_bins = S.w_nb; T.n_spec = S.w_ns; T.spec = S.spec;
     T.lnl_star = -INFINITY; T.iteration = 0; T.walker_offset = 0;
     T.key0 = S.key0; T.key1 = S.key1; T.n_s = S.n_live - S.k; T.n = S.k; T.n_steps = S.n_steps;
     T.done = 0; T.event = e;
@@ -518,8 +539,8 @@ void nested_free(ns_handle* h) {
   h->walk_events.clear();
   for (auto& E : h->events) {
     NsState& S = E.ns;
-    void* ptrs[] = {S.live_u, S.live_lnl, S.surv_u, S.w_u0, S.w_lnl0, S.w_uo, S.w_lo, S.w_na, S.w_nl,
-                    S.slot, S.w_nb, S.dead_u, S.dead_lnl, S.dead_logw, S.dead_nlive};
+    void* ptrs[] = {S.live_u, S.live_lnl, S.surv_u, S.surv32, S.w_u0, S.w_lnl0, S.w_uo, S.w_lo, S.w_na, S.w_nl,
+                    S.slot, S.w_nb, S.w_ns, S.dead_u, S.dead_lnl, S.dead_logw, S.dead_nlive};
     for (void* p : ptrs) cudaFree(p);
     std::memset(&S, 0, sizeof(S));
   }
@@ -546,6 +567,9 @@ static void fill_progress(ns_handle* h, ns_progress* p) {
     p[e].n_bins = S.n_bins_eval;
     p[e].walk_ms = h->walk_ms;
     p[e].kernel_launches = h->kernel_launches;
+    p[e].n_spec = S.n_spec_eval;
+    p[e].spec_depth = S.spec;
+    p[e].reserved = 0;
   }
 }
 
@@ -742,7 +766,7 @@ extern "C" int ns_state_load(ns_handle* h, const char* path) {
   for (int e = 0; e < ne; ++e) {
     NsState S = saved[e];
     const NsState& cur = h->events[e].ns;
-    S.live_u = cur.live_u; S.live_lnl = cur.live_lnl; S.surv_u = cur.surv_u;
+    S.live_u = cur.live_u; S.live_lnl = cur.live_lnl; S.surv_u = cur.surv_u; S.surv32 = cur.surv32;
     S.w_u0 = cur.w_u0; S.w_lnl0 = cur.w_lnl0; S.w_uo = cur.w_uo; S.w_lo = cur.w_lo;
     S.w_na = cur.w_na; S.w_nl = cur.w_nl; S.slot = cur.slot;
     S.dead_u = cur.dead_u; S.dead_lnl = cur.dead_lnl; S.dead_logw = cur.dead_logw; S.dead_nlive = cur.dead_nlive;
@@ -751,6 +775,7 @@ extern "C" int ns_state_load(ns_handle* h, const char* path) {
     WalkTask* dt = h->d_tasks + e;
     cudaMemcpy(&dt->done, &S.done, sizeof(int32_t), cudaMemcpyHostToDevice);
     cudaMemcpy(&dt->n_steps, &S.n_steps, sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(&dt->spec, &S.spec, sizeof(int32_t), cudaMemcpyHostToDevice);
   }
   return download_states(h);
 }

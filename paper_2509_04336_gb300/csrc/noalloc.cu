@@ -104,6 +104,7 @@ extern "C" int ns_walk_batch_noalloc(ns_handle* h, int event, const double* live
   T.n_steps = n_steps;
   T.done = 0;
   T.event = event;
+  T.spec = E.cfg.spec_depth > 0 ? E.cfg.spec_depth : default_spec(h->precision);
   cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
   fill_walk_scratch<<<(n + 255) / 256, 256, 0, s>>>(scratch, T, n);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "scratch fill launch");

@@ -23,6 +23,7 @@ MAX_DET = 4
 NS_OK, NS_EINVAL, NS_ECUDA, NS_ENOMEM, NS_ENONFINITE, NS_ETIMEOUT, NS_ESTATE, NS_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 NS_WMAXMCMC = 1
 NS_PTR_HOST, NS_PTR_DEVICE = 0, 1
+NS_PREC_FP64, NS_PREC_MIXED, NS_PREC_MIXED_FF = 0, 1, 2
 STATUS_NAMES = {0: "NS_OK", -1: "NS_EINVAL", -2: "NS_ECUDA", -3: "NS_ENOMEM", -4: "NS_ENONFINITE",
                 -5: "NS_ETIMEOUT", -6: "NS_ESTATE", -7: "NS_EIO", 1: "NS_WMAXMCMC"}
 
@@ -37,7 +38,7 @@ class ns_config(C.Structure):
                 ("naccept", C.c_int32), ("maxmcmc", C.c_int32), ("delay", C.c_double),
                 ("use_ratio", C.c_int32), ("term_kind", C.c_int32), ("term_value", C.c_double),
                 ("precision", C.c_int32), ("waveform", C.c_int32), ("max_iter", C.c_int32),
-                ("n_steps0", C.c_int32), ("seed", C.c_uint64)]
+                ("n_steps0", C.c_int32), ("seed", C.c_uint64), ("spec_depth", C.c_int32), ("reserved", C.c_int32)]
 
 
 class ns_detector(C.Structure):
@@ -54,7 +55,8 @@ class ns_progress(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("n_like", C.c_int64), ("log_z", C.c_double), ("dlogz", C.c_double),
                 ("log_x", C.c_double), ("lnl_star", C.c_double), ("mean_accept", C.c_double),
                 ("n_steps", C.c_int32), ("done", C.c_int32), ("n_bins", C.c_int64), ("walk_ms", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("n_spec", C.c_int64), ("spec_depth", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -133,7 +135,7 @@ def _same_kind(*arrays):
 
 # ---------------------------------------------------------------- marshalling helpers
 def make_config(w: synth.Workload, priors=None, *, precision=None, max_iter=0, n_steps0=0, delay=-1.0,
-                seed=None) -> ns_config:
+                seed=None, spec_depth=0) -> ns_config:
     c = ns_config()
     pri = w.priors if priors is None else priors
     for i, p in enumerate(pri):
@@ -146,6 +148,7 @@ def make_config(w: synth.Workload, priors=None, *, precision=None, max_iter=0, n
     c.waveform = w.waveform
     c.max_iter, c.n_steps0 = max_iter, n_steps0
     c.seed = w.seed if seed is None else seed
+    c.spec_depth = spec_depth
     return c
 
 

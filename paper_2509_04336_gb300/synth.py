@@ -39,7 +39,7 @@ UNIFORM, POWERLAW, SINE, COSINE, FIXED = 0, 1, 2, 3, 4
 KIND_NAMES = {UNIFORM: "uniform", POWERLAW: "powerlaw", SINE: "sine", COSINE: "cosine", FIXED: "fixed"}
 
 TAYLORF2, PHENOMD_FORM = 0, 1
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_FF = 0, 1, 2
 TERM_DLOGZ, TERM_FRAC_REMAINING = 0, 1
 
 EARTH_RADIUS_M = 6.371e6           # spherical Earth used for detector vertices

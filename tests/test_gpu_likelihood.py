@@ -53,6 +53,8 @@ def test_waveform_elementwise(name):
     ("four_param_2det_taylorf2", synth.PREC_MIXED, TOL_MIXED),
     ("bbh11_3det_4s_taylorf2", synth.PREC_FP64, TOL_FP64),
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED, TOL_MIXED),
+    ("four_param_2det_taylorf2", synth.PREC_MIXED_FF, TOL_MIXED),
+    ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, TOL_MIXED),
 ])
 def test_likelihood_parity(name, precision, tol):
     w, ev = event(name)
@@ -101,7 +103,7 @@ def test_likelihood_ragged_bins_small_event():
     # 23 bins: fewer than one CTA's threads, and a ragged tail.
     w, ev = event("bbh11_3det_4s_taylorf2", f_max=25.5)
     assert ev.n_bins == 23
-    for prec, tol in ((synth.PREC_FP64, TOL_FP64), (synth.PREC_MIXED, TOL_MIXED)):
+    for prec, tol in ((synth.PREC_FP64, TOL_FP64), (synth.PREC_MIXED, TOL_MIXED), (synth.PREC_MIXED_FF, TOL_MIXED)):
         h = handle(w, ev, prec)
         try:
             _, th = prior_draws(w, ev, 17, 3)

@@ -39,12 +39,16 @@ def walk_inputs(w, ev, n_surv, n_walk, seed):
     return ll, surv, np.ascontiguousarray(surv[starts]), np.ascontiguousarray(lnl_s[starts]), lnl_star
 
 
-@pytest.mark.parametrize("name,precision", [
-    ("four_param_2det_taylorf2", synth.PREC_FP64),
-    ("bbh11_3det_4s_taylorf2", synth.PREC_FP64),
-    ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED),
+@pytest.mark.parametrize("name,precision,spec", [
+    ("four_param_2det_taylorf2", synth.PREC_FP64, 1),
+    ("four_param_2det_taylorf2", synth.PREC_FP64, 3),
+    ("bbh11_3det_4s_taylorf2", synth.PREC_FP64, 8),
+    ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED, 32),
+    ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, 2),
+    ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, 32),
 ])
-def test_walk_parity(name, precision):
+def test_walk_parity(name, precision, spec):
+    # Any speculation depth gives the chain of the one-step-at-a-time walk.
     w, ev = event(name)
     ll, surv, u0, l0, lnl_star = walk_inputs(w, ev, 60, 24, 4)
     n_steps, it, off = 12, 3, 7
@@ -52,7 +56,7 @@ def test_walk_parity(name, precision):
     key = (w.seed, 0)
     ou, ol, oa, on, margin = walk.acceptance_walk(ll, u0, l0, lnl_star, surv, n_steps, periodic, key, it,
                                                   walker_ids=np.arange(24) + off)
-    cfg = gwns.make_config(w, priors(w, ev), precision=precision)
+    cfg = gwns.make_config(w, priors(w, ev), precision=precision, spec_depth=spec)
     h = gwns.ns_init([cfg], [ev])
     try:
         gu, gl = np.zeros_like(u0), np.zeros(24)
@@ -94,7 +98,8 @@ def test_walk_device_pointers_and_zero_steps():
         gwns.ns_free(h)
 
 
-def test_batches_match_oracle_fp64():
+@pytest.mark.parametrize("spec", [0, 1, 32])
+def test_batches_match_oracle_fp64(spec):
     # The whole batch pipeline (sort, deletion, evidence, starts, walk, insertion, retune)
     # on identical Philox streams: dead points and evidence agree after three batches.
     w, ev = event("four_param_2det_taylorf2")
@@ -103,7 +108,7 @@ def test_batches_match_oracle_fp64():
     batches = 3
     ref = nested.run_nested(ll, w.n_dim, w.n_live, w.num_delete, w.naccept, w.maxmcmc,
                             P.periodic_mask(pri), (w.seed, 0), max_iter=batches, n_replay=2)
-    cfg = gwns.make_config(w, pri, precision=synth.PREC_FP64, max_iter=batches)
+    cfg = gwns.make_config(w, pri, precision=synth.PREC_FP64, max_iter=batches, spec_depth=spec)
     h = gwns.ns_init([cfg], [ev])
     try:
         code, prog = gwns.ns_step(h, batches)
@@ -135,6 +140,7 @@ def test_handles_in_sequence_and_step_statistics():
             p = prog[0]
             assert p["iterations"] == 2 and p["kernel_launches"] == 6
             assert p["walk_ms"] > 0 and p["n_bins"] > 0
+            assert p["n_spec"] >= p["n_like"] - w.n_live and 1 <= p["spec_depth"] <= 32
             assert p["n_bins"] <= (p["n_like"] - w.n_live) * ev.n_bins
         finally:
             gwns.ns_free(h)

@@ -36,7 +36,7 @@ def _setup():
 def test_noalloc_walk_matches_walk_on_consecutive_calls():
     import torch
     w, ev, pri, surv, l0, u0, star = _setup()
-    h = gwns.ns_init([gwns.make_config(w, pri, precision=synth.PREC_MIXED)], [ev])
+    h = gwns.ns_init([gwns.make_config(w, pri, precision=synth.PREC_MIXED_FF)], [ev])
     try:
         T = lambda a, dt=torch.float64: torch.tensor(np.ascontiguousarray(a), device="cuda", dtype=dt)
         for call, (it, off, steps) in enumerate([(3, 0, 15), (4, 12, 9)]):
