@@ -112,8 +112,11 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
   E.n_det = in.n_det;
   E.n_bins = in.n_bins;
   const int nb = in.n_bins, nd = in.n_det;
-  std::vector<double> basis((size_t)nb * kBasis);
-  std::vector<float2> basis_ff((size_t)nb * kBasis);
+  const int nbas = c.waveform == NS_WAVEFORM_PHENOMD_FORM ? kBasisPD : kBasis;
+  std::vector<double> basis((size_t)nb * nbas);
+  std::vector<float2> basis_ff((size_t)nb * nbas);
+  std::vector<double> gw64((size_t)nd * nb);
+  std::vector<float> gw32((size_t)nd * nb);
   std::vector<double2> z64((size_t)nd * nb);
   std::vector<float2> z32((size_t)nd * nb);
   std::vector<double> pref((size_t)nd * nb);
@@ -121,7 +124,7 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
   for (int k = 0; k < nb; ++k) {
     double f = in.f_min + in.df * (double)k;
     double c3 = std::cbrt(f), lf = std::log(f);
-    double* g = &basis[(size_t)k * kBasis];
+    double* g = &basis[(size_t)k * nbas];
     g[0] = 1.0 / (f * c3 * c3);   // f^-5/3
     g[1] = 1.0 / f;               // f^-1
     g[2] = 1.0 / (c3 * c3);       // f^-2/3
@@ -130,9 +133,17 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
     g[5] = c3 * c3;               // f^2/3
     g[6] = lf;                    // ln f
     g[7] = c3 * lf;               // f^1/3 ln f
-    for (int j = 0; j < kBasis; ++j) {
+    if (nbas == kBasisPD) {
+      g[8] = f * c3;              // f^4/3
+      g[9] = f * c3 * c3;         // f^5/3
+      g[10] = f * f;              // f^2
+      g[11] = 1.0 / (f * f * f);  // f^-3
+      g[12] = std::pow(f, 0.75);  // f^3/4
+      g[13] = f;                  // f
+    }
+    for (int j = 0; j < nbas; ++j) {
       float hi = (float)g[j];
-      basis_ff[(size_t)k * kBasis + j] = make_float2(hi, (float)(g[j] - (double)hi));
+      basis_ff[(size_t)k * nbas + j] = make_float2(hi, (float)(g[j] - (double)hi));
     }
   }
   for (int d = 0; d < nd; ++d) {
@@ -146,6 +157,7 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
       z64[(size_t)d * nb + k] = make_double2(zr, zi);
       z32[(size_t)d * nb + k] = make_float2((float)zr, (float)zi);
       double term = w * a * a;                                      // 4 df f^-7/3 / S
+      gw64[(size_t)d * nb + k] = term;
       double y = term - runc, t = run + y;
       runc = (t - run) - y;
       run = t;
@@ -156,25 +168,36 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
       dd = t2;
     }
   }
+  // FP32 template-power weights scaled by a power of two so that the largest is ~1
+  double gmax = 0.0;
+  for (double v : gw64) gmax = std::fmax(gmax, v);
+  const double gscale = gmax > 0.0 ? std::ldexp(1.0, -std::ilogb(gmax)) : 1.0;
+  for (size_t i = 0; i < gw64.size(); ++i) gw32[i] = (float)(gw64[i] * gscale);
   // device copies
   cudaError_t err;
   if ((err = cudaMalloc(&E.d_basis64, basis.size() * sizeof(double))) != cudaSuccess ||
       (err = cudaMalloc(&E.d_basis_ff, basis_ff.size() * sizeof(float2))) != cudaSuccess ||
       (err = cudaMalloc(&E.d_z64, z64.size() * sizeof(double2))) != cudaSuccess ||
       (err = cudaMalloc(&E.d_z32, z32.size() * sizeof(float2))) != cudaSuccess ||
-      (err = cudaMalloc(&E.d_hh_prefix, pref.size() * sizeof(double))) != cudaSuccess)
+      (err = cudaMalloc(&E.d_hh_prefix, pref.size() * sizeof(double))) != cudaSuccess ||
+      (err = cudaMalloc(&E.d_gw64, gw64.size() * sizeof(double))) != cudaSuccess ||
+      (err = cudaMalloc(&E.d_gw32, gw32.size() * sizeof(float))) != cudaSuccess)
     return set_error(nullptr, NS_ENOMEM, "event %d: device allocation failed: %s", e, cudaGetErrorString(err));
   if ((err = cudaMemcpy(E.d_basis64, basis.data(), basis.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMemcpy(E.d_basis_ff, basis_ff.data(), basis_ff.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMemcpy(E.d_z64, z64.data(), z64.size() * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMemcpy(E.d_z32, z32.data(), z32.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (err = cudaMemcpy(E.d_hh_prefix, pref.data(), pref.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+      (err = cudaMemcpy(E.d_hh_prefix, pref.data(), pref.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(E.d_gw64, gw64.data(), gw64.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(E.d_gw32, gw32.data(), gw32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
     return set_error(nullptr, NS_ECUDA, "event %d: upload failed: %s", e, cudaGetErrorString(err));
 
   EventDev& D = E.dev;
   std::memset(&D, 0, sizeof(D));
   D.n_det = nd;
   D.n_bins = nb;
+  D.waveform = c.waveform;
+  D.n_basis = nbas;
   D.use_ratio = c.use_ratio ? 1 : 0;
   D.f_min = in.f_min;
   D.df = in.df;
@@ -219,6 +242,9 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
   D.z64 = E.d_z64;
   D.z32 = E.d_z32;
   D.hh_prefix = E.d_hh_prefix;
+  D.gw64 = E.d_gw64;
+  D.gw32 = E.d_gw32;
+  D.gw32_unscale = 1.0 / gscale;
   E.n_dim = nd_dim;
   return NS_OK;
 }
@@ -229,6 +255,10 @@ void free_event(EventHost& E) {
   cudaFree(E.d_z64);
   cudaFree(E.d_z32);
   cudaFree(E.d_hh_prefix);
+  cudaFree(E.d_gw64);
+  cudaFree(E.d_gw32);
+  E.d_gw64 = nullptr;
+  E.d_gw32 = nullptr;
   E.d_basis64 = nullptr;
   E.d_basis_ff = nullptr;
   E.d_z64 = nullptr;
@@ -251,8 +281,6 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
     if (ev[e].n_det != ev[0].n_det)
       return set_error(nullptr, NS_EINVAL, "every event of a handle needs the same number of detectors");
   }
-  if (cfg[0].waveform != NS_WAVEFORM_TAYLORF2)
-    return set_error(nullptr, NS_EINVAL, "waveform %d is not available in this build", cfg[0].waveform);
   cudaError_t e0 = cudaSetDevice(device);
   if (e0 != cudaSuccess) return set_error(nullptr, NS_ECUDA, "cudaSetDevice(%d): %s", device, cudaGetErrorString(e0));
   cudaGetLastError();   // a stale error of an earlier call must not be reported here
@@ -325,13 +353,13 @@ extern "C" int ns_waveform(ns_handle* h, int event, const double* theta, int n, 
     double* d_im = d_re + nh;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(d_th, theta, tb, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(h, e, "H2D theta");
-    if ((e = launch_waveform(E.n_det, d_ev, d_th, n, E.n_bins, d_re, d_im, s)) != cudaSuccess) return cuda_fail(h, e, "waveform launch");
+    if ((e = launch_waveform(h->waveform, E.n_det, d_ev, d_th, n, E.n_bins, d_re, d_im, s)) != cudaSuccess) return cuda_fail(h, e, "waveform launch");
     if ((e = cudaMemcpyAsync(h_re, d_re, sizeof(double) * nh, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(h, e, "D2H h_re");
     if ((e = cudaMemcpyAsync(h_im, d_im, sizeof(double) * nh, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(h, e, "D2H h_im");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "waveform");
     return NS_OK;
   }
-  cudaError_t e = launch_waveform(E.n_det, d_ev, theta, n, E.n_bins, h_re, h_im, s);
+  cudaError_t e = launch_waveform(h->waveform, E.n_det, d_ev, theta, n, E.n_bins, h_re, h_im, s);
   return e == cudaSuccess ? NS_OK : cuda_fail(h, e, "waveform launch");
 }
 
@@ -359,7 +387,7 @@ extern "C" int ns_likelihood_batch(ns_handle* h, int event, const double* theta,
     double* d_th = (double*)h->scratch_in.ptr;
     double* d_l = (double*)h->scratch_out.ptr;
     if ((e = cudaMemcpyAsync(d_th, theta, tb, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(h, e, "H2D theta");
-    if ((e = launch_likelihood(h->precision, E.n_det, d_ev, d_th, n, d_l, h->d_status, s)) != cudaSuccess)
+    if ((e = launch_likelihood(h->precision, h->waveform, E.n_det, d_ev, d_th, n, d_l, h->d_status, s)) != cudaSuccess)
       return cuda_fail(h, e, "likelihood launch");
     if ((e = cudaMemcpyAsync(lnl, d_l, sizeof(double) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(h, e, "D2H lnl");
     int32_t st = 0;
@@ -368,7 +396,7 @@ extern "C" int ns_likelihood_batch(ns_handle* h, int event, const double* theta,
     if (st) return set_error(h, NS_ENONFINITE, "a theta was not finite or out of the physical domain");
     return NS_OK;
   }
-  e = launch_likelihood(h->precision, E.n_det, d_ev, theta, n, lnl, h->d_status, s);
+  e = launch_likelihood(h->precision, h->waveform, E.n_det, d_ev, theta, n, lnl, h->d_status, s);
   return e == cudaSuccess ? NS_OK : cuda_fail(h, e, "likelihood launch");
 }
 
@@ -433,7 +461,7 @@ extern "C" int ns_walk_batch(ns_handle* h, int event, const double* live_u, int 
         (e = cudaMemcpyAsync(d_task, &T, sizeof(T), cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(d_be, maps.data(), sizeof(int32_t) * 2 * n, cudaMemcpyHostToDevice, s)))
       return cuda_fail(h, e, "H2D walk inputs");
-    if ((e = launch_walk(h->precision, E.n_det, h->d_events, d_task, d_be, d_bl, n, s)) != cudaSuccess)
+    if ((e = launch_walk(h->precision, h->waveform, E.n_det, h->d_events, d_task, d_be, d_bl, n, s)) != cudaSuccess)
       return cuda_fail(h, e, "walk launch");
     if ((e = cudaMemcpyAsync(u_out, d_uo, sizeof(double) * nu, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(lnl_out, d_lo, sizeof(double) * n, cudaMemcpyDeviceToHost, s)) ||
@@ -451,7 +479,7 @@ extern "C" int ns_walk_batch(ns_handle* h, int event, const double* live_u, int 
   stage.insert(stage.end(), (char*)maps.data(), (char*)maps.data() + sizeof(int32_t) * 2 * n);
   if ((e = cudaMemcpyAsync(d_task, stage.data(), stage.size(), cudaMemcpyHostToDevice, s)))
     return cuda_fail(h, e, "H2D walk task");
-  e = launch_walk(h->precision, E.n_det, h->d_events, d_task, d_be, d_bl, n, s);
+  e = launch_walk(h->precision, h->waveform, E.n_det, h->d_events, d_task, d_be, d_bl, n, s);
   return e == cudaSuccess ? NS_OK : cuda_fail(h, e, "walk launch");
 }
 

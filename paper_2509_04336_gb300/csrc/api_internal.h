@@ -53,6 +53,8 @@ struct EventHost {
   double2* d_z64 = nullptr;
   float2* d_z32 = nullptr;
   double* d_hh_prefix = nullptr;
+  double* d_gw64 = nullptr;
+  float* d_gw32 = nullptr;
   NsState ns;            // host mirror of the device pointers and static fields
 };
 

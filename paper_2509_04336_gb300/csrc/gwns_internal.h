@@ -38,18 +38,18 @@ struct WalkTask {
 
 constexpr int kSpecMax = 32;   // speculation depth limit (one warp of proposals)
 
-// Launch wrappers (kernels.cu).  Every wrapper returns the launch error.
-cudaError_t launch_likelihood(int precision, int n_det, const EventDev* d_ev, const double* d_theta,
+// Launch wrappers (kernels.cu).  Every wrapper returns the launch error.  precision:
+// NS_PREC_*; waveform: NS_WAVEFORM_*.
+cudaError_t launch_likelihood(int precision, int waveform, int n_det, const EventDev* d_ev, const double* d_theta,
                               int n, double* d_lnl, int32_t* d_status, cudaStream_t s);
-cudaError_t launch_waveform(int n_det, const EventDev* d_ev, const double* d_theta, int n, int n_bins,
-                            double* d_hre, double* d_him, cudaStream_t s);
-cudaError_t launch_unit_likelihood(int precision, int n_det, const EventDev* d_ev, const double* d_u, int n,
-                                   double* d_lnl, cudaStream_t s);
+cudaError_t launch_unit_likelihood(int precision, int waveform, int n_det, const EventDev* d_ev, const double* d_u,
+                                   int n, double* d_lnl, cudaStream_t s);
 cudaError_t launch_unit_to_theta(const EventDev* d_ev, const double* d_u, int64_t n, double* d_theta,
                                  cudaStream_t s);
+cudaError_t launch_waveform(int waveform, int n_det, const EventDev* d_ev, const double* d_theta, int n, int n_bins,
+                            double* d_hre, double* d_him, cudaStream_t s);
 // Block b walks walker blk_local[b] of task blk_task[b].
-cudaError_t launch_walk(int precision, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
-                        const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks,
-                        cudaStream_t s);
+cudaError_t launch_walk(int precision, int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
+                        const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s);
 
 }  // namespace gwns

@@ -23,7 +23,7 @@ namespace gwns {
 constexpr int kParams = 11;
 constexpr int kMaxDet = 4;
 constexpr int kMaxDim = 11;
-constexpr int kBasis = 8;
+constexpr int kBasis = 8;        // TaylorF2 phase basis
 
 // SI constants: exact c, IAU 2015 nominal solar mass parameter, IAU parsec.
 constexpr double kC = 299792458.0;
@@ -35,6 +35,15 @@ constexpr double kEulerGamma = 0.5772156649015329;
 constexpr double kLn4 = 1.3862943611198906;
 constexpr double kSix15 = 14.696938456699069;   // 6^(3/2)
 constexpr double kAmp0 = 0.21278751013966343;   // sqrt(5/24) pi^(-2/3)
+
+struct EventDev;
+struct WalkerParams;
+struct PhenomExtra;
+// IMRPhenomD-form constants of a proposal (gwns_phenomd.cuh), called by the setups below.
+template <bool FAST>
+__device__ void phenomd_extra(const EventDev& ev, WalkerParams& p, PhenomExtra& e, double eta, double delta,
+                              double chis, double chia, const double* a, const double* al, double c1, double lpm,
+                              double q, double chi1, double chi2, double phic);
 
 enum PriorKind { kUniform = 0, kPowerLaw = 1, kSine = 2, kCosine = 3, kFixed = 4 };
 
@@ -53,6 +62,7 @@ struct PriorDev {
 // Device copy of one event and its sampler configuration.
 struct EventDev {
   int n_det, n_bins, n_dim, use_ratio;
+  int waveform, n_basis;               // 0 TaylorF2 (8 basis functions), 1 IMRPhenomD form (14)
   double f_min, df, gmst;
   double dd_total;                     // sum_det <d|d>
   double vertex[kMaxDet][3], xarm[kMaxDet][3], yarm[kMaxDet][3];
@@ -64,6 +74,23 @@ struct EventDev {
   const double2* z64;                  // [n_det][n_bins]
   const float2* z32;                   // [n_det][n_bins]
   const double* hh_prefix;             // [n_det][n_bins] inclusive prefix sums of 4 df f^-7/3 / S
+  const double* gw64;                  // [n_det][n_bins] 4 df f^-7/3 / S (per-bin template power)
+  const float* gw32;                   // [n_det][n_bins] FP32 copy scaled by 1/gw32_unscale (a power
+                                       //   of two: the weights reach ~1e43, beyond FP32's range)
+  double gw32_unscale;
+};
+
+// The IMRPhenomD-form part of the per-walker constants (in cycles).
+struct PhenomExtra {
+  double Cx[9];         // ins: f^4/3 f^5/3 f^2 | int: ln f, f^-3, f | mr: f^-1, f^3/4, f
+  double ph0_int, ph0_mr;
+  float Cxh[9], Cxl[9];
+  float ph0_int_h, ph0_int_l, ph0_mr_h, ph0_mr_l;
+  int k1, k2, ka, kp;   // first bins of: intermediate phase, MR phase, intermediate amp, MR amp
+  // amplitude shape and the ringdown atan term, FP64 (FP64 path) and FP32 (mixed paths)
+  double A2, A3, c13, M, xa, inv_span, hy0, hd0, hc2, hc3, frd, gd, g1gd, g2_gd, at_scale, at_c, at_inv;
+  float A2f, A3f, c13f, Mf, xaf, inv_spanf, hy0f, hd0f, hc2f, hc3f, frdf, gdf, g1gdf, g2_gdf, at_scalef, at_cf,
+      at_invf;
 };
 
 // Per-walker constants of one likelihood evaluation.  The float fields are the
@@ -80,6 +107,7 @@ struct WalkerParams {
   float ph0h, ph0l;                    // phase0 = ph0h + ph0l
   float sa[kMaxDet];                   // frac(tau f_min)                       [cycles]
   float sbh[kMaxDet], sbl[kMaxDet];    // tau df = sbh + sbl, sbh with 9 significant bits
+  PhenomExtra pd;                      // IMRPhenomD-form regions (unused for TaylorF2)
 };
 
 // ---------------------------------------------------------------- Philox4x64-10
@@ -211,7 +239,9 @@ __device__ inline void detector_response(const EventDev& ev, int det, double sp,
   *dt = -(r[0] * n0 + r[1] * n1 + r[2] * n2) / kC;
 }
 
-// Per-walker constants for theta (with cos iota, sin dec, cos dec supplied).
+// Per-walker constants for theta (with cos iota, sin dec, cos dec supplied); WF 1 adds the
+// IMRPhenomD-form regions.
+template <int WF>
 __device__ inline void taylorf2_setup(const EventDev& ev, const double* th, double ci, double sdec,
                                       double cdec, WalkerParams& p) {
   double mc = th[0], q = th[1], chi1 = th[2], chi2 = th[3], dl = th[4];
@@ -240,6 +270,7 @@ __device__ inline void taylorf2_setup(const EventDev& ev, const double* th, doub
   p.C[6] = pre * al[5] / 3.0;
   p.C[7] = pre * c1 * al[6] / 3.0;
   p.phase0 = pre * (a[5] + al[5] * lpm / 3.0) - phic / kPi - 0.125;
+  if (WF == 1) phenomd_extra<false>(ev, p, p.pd, eta, delta, chis, chia, a, al, c1, lpm, q, chi1, chi2, phic);
 
   // restricted amplitude K = sqrt(5/24) pi^(-2/3) (G Mc/c^3)^(5/6) / (d_L/c)
   double mcs = mc * kMsunS;
@@ -257,7 +288,7 @@ __device__ inline void taylorf2_setup(const EventDev& ev, const double* th, doub
     p.kp_re[det] = K * pre_re;
     p.kp_im[det] = K * pre_im;
     p.tau[det] = tc + dt;
-    double psum = p.k_end > 0 ? ev.hh_prefix[(size_t)det * ev.n_bins + p.k_end - 1] : 0.0;
+    double psum = (WF == 0 && p.k_end > 0) ? ev.hh_prefix[(size_t)det * ev.n_bins + p.k_end - 1] : 0.0;
     hh += K * K * (pre_re * pre_re + pre_im * pre_im) * psum;
   }
   p.hh = hh;
@@ -265,6 +296,7 @@ __device__ inline void taylorf2_setup(const EventDev& ev, const double* th, doub
 
 // Float-float split of the per-walker constants.  k * sbh is exact in FP32 for k < 2^15
 // because sbh keeps 9 significant bits, so the time-shift phase k tau df is reduced exactly.
+template <int WF>
 __device__ inline void make_ff(const EventDev& ev, WalkerParams& p) {
   for (int j = 0; j < kBasis; ++j) {
     float h = (float)p.C[j];
@@ -274,6 +306,20 @@ __device__ inline void make_ff(const EventDev& ev, WalkerParams& p) {
   float h0 = (float)p.phase0;
   p.ph0h = h0;
   p.ph0l = (float)(p.phase0 - (double)h0);
+  if (WF == 1) {
+    PhenomExtra& e = p.pd;
+    for (int j = 0; j < 9; ++j) {
+      float h = (float)e.Cx[j];
+      e.Cxh[j] = h;
+      e.Cxl[j] = (float)(e.Cx[j] - (double)h);
+    }
+    float h = (float)e.ph0_int;
+    e.ph0_int_h = h;
+    e.ph0_int_l = (float)(e.ph0_int - (double)h);
+    h = (float)e.ph0_mr;
+    e.ph0_mr_h = h;
+    e.ph0_mr_l = (float)(e.ph0_mr - (double)h);
+  }
   for (int det = 0; det < ev.n_det; ++det) {
     double a = p.tau[det] * ev.f_min;
     p.sa[det] = (float)(a - rint(a));
@@ -357,6 +403,7 @@ __device__ inline void unit_to_lean(const EventDev& ev, const double* u, LeanThe
   t.phic = x[7]; t.tc = x[8]; t.ra = x[9]; t.sdec = sd; t.cdec = cd;
 }
 
+template <int WF>
 __device__ inline void taylorf2_setup_lean(const EventDev& ev, const LeanTheta& t, WalkerParams& p) {
   const double q = t.q;
   const double opq = 1.0 + q;
@@ -386,6 +433,8 @@ __device__ inline void taylorf2_setup_lean(const EventDev& ev, const LeanTheta& 
   p.C[6] = pre * al[5] / 3.0;
   p.C[7] = pre * c1 * al[6] / 3.0;
   p.phase0 = pre * (a[5] + al[5] * lpm / 3.0) - t.phic / kPi - 0.125;
+  if (WF == 1)
+    phenomd_extra<true>(ev, p, p.pd, eta, delta, chis, chia, a, al, c1, lpm, q, t.chi1, t.chi2, t.phic);
   // sky direction in FP64 (it sets the arrival delays), the rest in FP32
   double sp, cp;
   sincos(t.ra - ev.gmst, &sp, &cp);
@@ -411,7 +460,7 @@ __device__ inline void taylorf2_setup_lean(const EventDev& ev, const LeanTheta& 
     p.kp_im[det] = (double)(K * pi_);
     const double* r = ev.vertex[det];
     p.tau[det] = t.tc - (r[0] * n0 + r[1] * n1 + r[2] * n2) * (1.0 / kC);
-    double psum = p.k_end > 0 ? ev.hh_prefix[(size_t)det * ev.n_bins + p.k_end - 1] : 0.0;
+    double psum = (WF == 0 && p.k_end > 0) ? ev.hh_prefix[(size_t)det * ev.n_bins + p.k_end - 1] : 0.0;
     // K ~ 1e-21: its square underflows FP32, so |K P|^2 is formed in FP64
     hh += (p.kp_re[det] * p.kp_re[det] + p.kp_im[det] * p.kp_im[det]) * psum;
   }
@@ -451,7 +500,7 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 template <int NDET>
 __device__ __forceinline__ void bin_accumulate_f64(const EventDev& ev, const WalkerParams& p, int k,
                                                    AccF64& acc) {
-  const double* g = ev.basis64 + (size_t)k * kBasis;
+  const double* g = ev.basis64 + (size_t)k * ev.n_basis;
   double phi = p.phase0;
 #pragma unroll
   for (int j = 0; j < kBasis; ++j) phi = fma(p.C[j], g[j], phi);
@@ -473,7 +522,7 @@ __device__ __forceinline__ void bin_accumulate_f64(const EventDev& ev, const Wal
 template <int NDET>
 __device__ __forceinline__ void bin_accumulate_mixed(const EventDev& ev, const WalkerParams& p, int k,
                                                      AccF32& acc) {
-  const double* g = ev.basis64 + (size_t)k * kBasis;
+  const double* g = ev.basis64 + (size_t)k * ev.n_basis;
   double phi = p.phase0;
 #pragma unroll
   for (int j = 0; j < kBasis; ++j) phi = fma(p.C[j], g[j], phi);
@@ -496,7 +545,7 @@ __device__ __forceinline__ void bin_accumulate_mixed(const EventDev& ev, const W
 template <int NDET>
 __device__ __forceinline__ void bin_accumulate_ff(const EventDev& ev, const WalkerParams& p, int k,
                                                   AccF32& acc) {
-  const float2* g = ev.basis_ff + (size_t)k * kBasis;
+  const float2* g = ev.basis_ff + (size_t)k * ev.n_basis;
   float sh = p.ph0h, sl = p.ph0l;
 #pragma unroll
   for (int j = 0; j < kBasis; ++j) {
@@ -528,12 +577,21 @@ __device__ __forceinline__ void bin_accumulate_ff(const EventDev& ev, const Walk
 }
 
 // ln L from the reduced sums S_det (FP64 assembly).
+// s_hh: per-detector accumulated template power (IMRPhenomD form; ignored for TaylorF2, whose
+// <h|h> comes from the prefix sums).
 __device__ inline double assemble_lnl(const EventDev& ev, const WalkerParams& p, const double* s_re,
-                                      const double* s_im) {
-  double dh = 0.0;
+                                      const double* s_im, const double* s_hh = nullptr) {
+  double dh = 0.0, hh = p.hh;
   for (int det = 0; det < ev.n_det; ++det) dh += p.kp_re[det] * s_re[det] - p.kp_im[det] * s_im[det];
-  if (ev.use_ratio) return dh - 0.5 * p.hh;
-  return -0.5 * (ev.dd_total - 2.0 * dh + p.hh);
+  if (ev.waveform == 1 && s_hh) {
+    hh = 0.0;
+    for (int det = 0; det < ev.n_det; ++det)
+      hh += (p.kp_re[det] * p.kp_re[det] + p.kp_im[det] * p.kp_im[det]) * s_hh[det];
+  }
+  if (ev.use_ratio) return dh - 0.5 * hh;
+  return -0.5 * (ev.dd_total - 2.0 * dh + hh);
 }
 
 }  // namespace gwns
+
+#include "gwns_phenomd.cuh"

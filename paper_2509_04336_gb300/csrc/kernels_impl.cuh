@@ -1,0 +1,593 @@
+// kernels_impl.cuh -- likelihood, waveform and acceptance-walk kernels (sm_103a).
+// Included by kernels_p{0,1,2}.cu, one translation unit per precision (parallel builds).
+//
+// Template parameters of every kernel: PREC (0 FP64, 1 mixed with FP64 phase, 2 mixed with
+// float-float phase), NDET (detectors, 1..4) and WF (0 TaylorF2, 1 IMRPhenomD form).
+// Per-bin sums per detector: Re and Im of S_det = sum_k a_k z_k exp(-2 pi i Phi_det(f_k)), and
+// for the IMRPhenomD form the template power sum_k a_k^2 4 df f^-7/3 / S (TaylorF2 takes it
+// from prefix sums).  Threads accumulate disjoint bin subsets (FP64, or FP32 with Kahan
+// compensation), then warp-shuffle trees (error-free two-sums in FP32) reduce them.
+#pragma once
+
+#include <cstdio>
+
+#include "gwns_internal.h"
+
+namespace gwns {
+
+namespace {
+
+// Per-SM arrival counters of walk CTAs.  A CTA's position modulo kThreads/32 picks the warp
+// that runs its per-proposal setup, so the CTAs sharing an SM spread that FP64-heavy work
+// over different sub-partitions (warp w of a CTA runs on sub-partition w mod 4).
+__device__ unsigned int g_walk_sm_arrivals[256];
+
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxVals = 3 * kMaxDet;   // (re, im, hh) per detector
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <int NDET, int WF>
+struct NVals { static constexpr int value = (WF == 1 ? 3 : 2) * NDET; };
+
+// Partial sums of the bins k = start, start + stride, ... of one walker (values laid out
+// [det][re, im(, hh)]).  FP64 path: dv; mixed paths: (fv, fc) Kahan pairs, fc the negated error.
+template <int PREC, int NDET, int WF>
+__device__ inline void partials(const EventDev& ev, const WalkerParams& P, int start, int stride, double* dv,
+                                float* fv, float* fc) {
+  constexpr int NW = (WF == 1 ? 3 : 2);
+  if (WF == 0) {
+    if (PREC == 0) {
+      AccF64 acc; acc.zero();
+      for (int k = start; k < P.k_end; k += stride) bin_accumulate_f64<NDET>(ev, P, k, acc);
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) { dv[NW * d] = acc.re[d]; dv[NW * d + 1] = acc.im[d]; }
+    } else {
+      AccF32 acc; acc.zero();
+      if (PREC == 1) {
+        for (int k = start; k < P.k_end; k += stride) bin_accumulate_mixed<NDET>(ev, P, k, acc);
+      } else {
+        for (int k = start; k < P.k_end; k += stride) bin_accumulate_ff<NDET>(ev, P, k, acc);
+      }
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        fv[NW * d] = acc.re[d]; fc[NW * d] = -acc.cre[d];
+        fv[NW * d + 1] = acc.im[d]; fc[NW * d + 1] = -acc.cim[d];
+      }
+    }
+  } else {
+    if (PREC == 0) {
+      AccPD64 acc; acc.zero();
+      for (int k = start; k < P.k_end; k += stride) pd_accumulate_f64<NDET>(ev, P, P.pd, k, acc);
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) { dv[NW * d] = acc.re[d]; dv[NW * d + 1] = acc.im[d]; dv[NW * d + 2] = acc.hh[d]; }
+    } else {
+      AccPD32 acc; acc.zero();
+      if (PREC == 1) {
+        for (int k = start; k < P.k_end; k += stride) pd_accumulate_mixed<NDET>(ev, P, P.pd, k, acc);
+      } else {
+        for (int k = start; k < P.k_end; k += stride) pd_accumulate_ff<NDET>(ev, P, P.pd, k, acc);
+      }
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        fv[NW * d] = acc.re[d]; fc[NW * d] = -acc.cre[d];
+        fv[NW * d + 1] = acc.im[d]; fc[NW * d + 1] = -acc.cim[d];
+        fv[NW * d + 2] = acc.hh[d]; fc[NW * d + 2] = -acc.chh[d];
+      }
+    }
+  }
+}
+
+// Warp reductions: lane 0 receives the totals.
+template <int NV>
+__device__ __forceinline__ void warp_reduce_f64(double* dv) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double r = dv[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
+    dv[i] = r;
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void warp_reduce_f32(float* fv, float* fc) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    float s = fv[i], c = fc[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      float so = __shfl_down_sync(0xffffffffu, s, off);
+      float co = __shfl_down_sync(0xffffffffu, c, off);
+      float t, e;
+      two_sum(s, so, t, e);
+      s = t;
+      c = c + co + e;
+    }
+    fv[i] = s;
+    fc[i] = c;
+  }
+}
+
+// Sums of one walker over the whole CTA (stride kThreads), totals in `out` for thread 0.
+template <int PREC, int NDET, int WF>
+__device__ inline void cta_sums(const EventDev& ev, const WalkerParams& P, double (*red)[kMaxVals], double* out) {
+  constexpr int NV = NVals<NDET, WF>::value;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double dv[NV];
+  float fv[NV], fc[NV];
+  partials<PREC, NDET, WF>(ev, P, threadIdx.x, kThreads, dv, fv, fc);
+  if (PREC == 0) {
+    warp_reduce_f64<NV>(dv);
+    if (lane == 0) for (int i = 0; i < NV; ++i) red[warp][i] = dv[i];
+  } else {
+    warp_reduce_f32<NV>(fv, fc);
+    if (lane == 0) for (int i = 0; i < NV; ++i) red[warp][i] = (double)fv[i] + (double)fc[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NV; ++i) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += red[w][i];
+      out[i] = t;
+    }
+  }
+}
+
+// ln L from reduced values laid out [det][re, im(, hh)]; the mixed paths' template-power sums
+// are in units of the scaled FP32 weights.
+template <int PREC, int NDET, int WF>
+__device__ inline double lnl_from_vals(const EventDev& ev, const WalkerParams& P, const double* v) {
+  constexpr int NW = (WF == 1 ? 3 : 2);
+  double sr[kMaxDet], si[kMaxDet], sh[kMaxDet];
+  const double hscale = PREC == 0 ? 1.0 : ev.gw32_unscale;
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    sr[d] = v[NW * d];
+    si[d] = v[NW * d + 1];
+    sh[d] = (WF == 1) ? v[NW * d + 2] * hscale : 0.0;
+  }
+  return assemble_lnl(ev, P, sr, si, WF == 1 ? sh : nullptr);
+}
+
+__device__ inline bool theta_ok(const double* th) {
+  for (int i = 0; i < kParams; ++i) if (!isfinite(th[i])) return false;
+  return th[0] > 0.0 && th[1] > 0.0 && th[4] > 0.0;
+}
+
+// Per-walker constants of one proposal: the FP64 path uses the plain FP64 setup, the mixed
+// paths the lean one (FP64 only where the phase needs it).
+template <int PREC, int WF>
+__device__ inline void setup_from_unit(const EventDev& ev, const double* u, WalkerParams& P) {
+  if (PREC == 0) {
+    double th[kParams], ci, sd, cd;
+    unit_to_theta(ev, u, th, &ci, &sd, &cd);
+    taylorf2_setup<WF>(ev, th, ci, sd, cd, P);
+  } else {
+    LeanTheta t;
+    unit_to_lean(ev, u, t);
+    taylorf2_setup_lean<WF>(ev, t, P);
+    if (PREC == 2) make_ff<WF>(ev, P);
+  }
+}
+
+template <int PREC, int WF>
+__device__ inline void setup_from_theta(const EventDev& ev, const double* th, WalkerParams& P) {
+  if (PREC == 0) {
+    double sd, cd;
+    sincos(th[10], &sd, &cd);
+    taylorf2_setup<WF>(ev, th, cos(th[5]), sd, cd, P);
+  } else {
+    LeanTheta t;
+    theta_to_lean(th, t);
+    taylorf2_setup_lean<WF>(ev, t, P);
+    if (PREC == 2) make_ff<WF>(ev, P);
+  }
+}
+
+// ---------------------------------------------------------------- likelihood batch
+template <int PREC, int NDET, int WF>
+__global__ void __launch_bounds__(kThreads) likelihood_kernel(const EventDev* __restrict__ evp,
+                                                               const double* __restrict__ theta, int n,
+                                                               double* __restrict__ lnl, int32_t* status) {
+  __shared__ WalkerParams P;
+  __shared__ double red[kWarps][kMaxVals];
+  __shared__ double vals[kMaxVals];
+  __shared__ int ok;
+  const EventDev& ev = *evp;
+  const int w = blockIdx.x;
+  if (threadIdx.x == 0) {
+    double th[kParams];
+    for (int i = 0; i < kParams; ++i) th[i] = theta[(size_t)w * kParams + i];
+    ok = theta_ok(th);
+    if (ok) setup_from_theta<PREC, WF>(ev, th, P);
+    else P.k_end = 0;
+  }
+  __syncthreads();
+  cta_sums<PREC, NDET, WF>(ev, P, red, vals);
+  if (threadIdx.x == 0) {
+    if (ok) {
+      lnl[w] = lnl_from_vals<PREC, NDET, WF>(ev, P, vals);
+    } else {
+      lnl[w] = __longlong_as_double(0x7ff8000000000000ll);
+      atomicOr(status, 1);
+    }
+  }
+}
+
+// ln L of unit-cube points u [n][D] (prior transform, then the likelihood).  Used for the
+// initial live points; non-finite results are stored as -inf so that they die first.
+template <int PREC, int NDET, int WF>
+__global__ void __launch_bounds__(kThreads) unit_likelihood_kernel(const EventDev* __restrict__ evp,
+                                                                    const double* __restrict__ u, int n,
+                                                                    double* __restrict__ lnl) {
+  __shared__ WalkerParams P;
+  __shared__ double red[kWarps][kMaxVals];
+  __shared__ double vals[kMaxVals];
+  const EventDev& ev = *evp;
+  const int w = blockIdx.x;
+  if (threadIdx.x == 0) setup_from_unit<PREC, WF>(ev, u + (size_t)w * ev.n_dim, P);
+  __syncthreads();
+  cta_sums<PREC, NDET, WF>(ev, P, red, vals);
+  if (threadIdx.x == 0) {
+    double v = lnl_from_vals<PREC, NDET, WF>(ev, P, vals);
+    lnl[w] = isfinite(v) ? v : -INFINITY;
+  }
+}
+
+// Physical theta [n][11] of unit-cube points u [n][D].
+__global__ void unit_to_theta_kernel(const EventDev* __restrict__ evp, const double* __restrict__ u, int64_t n,
+                                     double* __restrict__ theta) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const EventDev& ev = *evp;
+  double th[kParams], ci, sd, cd;
+  unit_to_theta(ev, u + i * ev.n_dim, th, &ci, &sd, &cd);
+  for (int k = 0; k < kParams; ++k) theta[i * kParams + k] = th[k];
+}
+
+// ---------------------------------------------------------------- waveform (FP64)
+template <int NDET, int WF>
+__global__ void __launch_bounds__(256) waveform_kernel(const EventDev* __restrict__ evp,
+                                                       const double* __restrict__ theta, int n_bins,
+                                                       double* __restrict__ h_re, double* __restrict__ h_im) {
+  __shared__ WalkerParams P;
+  const EventDev& ev = *evp;
+  const int w = blockIdx.y;
+  if (threadIdx.x == 0) {
+    double th[kParams];
+    for (int i = 0; i < kParams; ++i) th[i] = theta[(size_t)w * kParams + i];
+    setup_from_theta<0, WF>(ev, th, P);
+  }
+  __syncthreads();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_bins) return;
+  const double f = ev.f_min + ev.df * (double)k;
+  double phi = 0.0, amp = 0.0;
+  if (k < P.k_end) {
+    const double* g = ev.basis64 + (size_t)k * ev.n_basis;
+    if (WF == 0) {
+      phi = P.phase0;
+      for (int j = 0; j < kBasis; ++j) phi = fma(P.C[j], g[j], phi);
+      amp = 1.0;
+    } else {
+      const PhenomExtra& e = P.pd;
+      if (k < e.k1) {
+        phi = P.phase0;
+        for (int j = 0; j < kBasis; ++j) phi = fma(P.C[j], g[j], phi);
+        phi = fma(e.Cx[0], g[8], fma(e.Cx[1], g[9], fma(e.Cx[2], g[10], phi)));
+      } else if (k < e.k2) {
+        phi = fma(e.Cx[3], g[6], fma(e.Cx[4], g[11], fma(e.Cx[5], g[13], e.ph0_int)));
+      } else {
+        phi = fma(e.Cx[6], g[1], fma(e.Cx[7], g[12], fma(e.Cx[8], g[13], e.ph0_mr)));
+        phi += e.at_scale * atan((e.M * f - e.at_c) * e.at_inv);
+      }
+      amp = pd_amp_f64(e, k, f, g[4]);
+    }
+  }
+  const double a7 = pow(f, -7.0 / 6.0) * amp;
+#pragma unroll
+  for (int det = 0; det < NDET; ++det) {
+    double re = 0.0, im = 0.0;
+    if (k < P.k_end) {
+      double ph = fma(P.tau[det], f, phi);
+      double r = ph - rint(ph);
+      double s, c;
+      sincospi(2.0 * r, &s, &c);
+      // a f^-7/6 K P exp(-2 pi i r)
+      re = a7 * (P.kp_re[det] * c + P.kp_im[det] * s);
+      im = a7 * (P.kp_im[det] * c - P.kp_re[det] * s);
+    }
+    size_t o = ((size_t)w * NDET + det) * n_bins + k;
+    h_re[o] = re;
+    h_im[o] = im;
+  }
+}
+
+// ---------------------------------------------------------------- acceptance walk
+// One CTA per walker, persistent over the walk.  A round looks ahead over the next W steps:
+//  1. the DE draws of a step depend only on its Philox counter (step, walker, iteration,
+//     tag), not on the chain, so every thread screens one candidate step in FP32 from the
+//     current position; the candidates that may lie in the cube are compacted into one warp,
+//     which redoes their draws and proposals exactly in FP64 and compacts the in-bounds ones,
+//     in step order, into at most m = task.spec slots;
+//  2. that warp computes the per-proposal constants (the FP64-heavy part) on full lanes, and
+//     the CTA evaluates the slots' likelihoods, one warp per proposal (the whole CTA per
+//     proposal when there are fewer than kWarps of them);
+//  3. thread 0 replays the steps in order: out-of-bounds steps reject without a likelihood
+//     call, the first in-bounds proposal with ln L > ln L* is taken and ends the round.
+//     Candidates after it were built from a position the chain has left and are redrawn
+//     from the new one in the next round.
+// The chain, the accepted and likelihood-call counts and every ln L are those of the walk
+// that takes one step at a time.  The setup warp rotates over the CTAs of an SM (an arrival
+// counter), so their FP64 work lands on different sub-partitions.
+template <int PREC, int NDET, int WF>
+__global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __restrict__ evs, WalkTask* tasks,
+                                                         const int32_t* __restrict__ blk_task,
+                                                         const int32_t* __restrict__ blk_local) {
+  constexpr int NV = NVals<NDET, WF>::value;
+  __shared__ WalkerParams P[kSpecMax];
+  __shared__ double prop[kSpecMax][kMaxDim];
+  __shared__ int cstep[kSpecMax];
+  __shared__ int mstep[32];
+  __shared__ double lnl_p[kSpecMax];
+  __shared__ float part_sums[kSpecMax][2 * kMaxVals];
+  __shared__ double u[kMaxDim];
+  __shared__ float u32[kMaxDim];
+  __shared__ double red[kWarps][kMaxVals];
+  __shared__ double vals[kMaxVals];
+  __shared__ int wcount[kWarps];
+  __shared__ int s_next, s_setup_warp, s_nin, s_end;
+  const WalkTask& T = tasks[blk_task[blockIdx.x]];
+  const int j = blk_local[blockIdx.x];
+  const EventDev& ev = evs[T.event];
+  if (T.done) return;
+  const int D = ev.n_dim;
+  const int n_steps = T.n_steps;
+  const double lnl_star = T.lnl_star;
+  const uint64_t it = (uint64_t)T.iteration;
+  const uint64_t wid = (uint64_t)(T.walker_offset + j);
+  const uint64_t n_s = (uint64_t)T.n_s;
+  const int m = T.spec < 1 ? 1 : (T.spec > kSpecMax ? kSpecMax : T.spec);
+  const int window = min(kThreads, max(32, 4 * m));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < D) {
+    u[threadIdx.x] = T.u0[(size_t)j * D + threadIdx.x];
+    u32[threadIdx.x] = (float)u[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    unsigned int smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    s_setup_warp = (int)(atomicAdd(&g_walk_sm_arrivals[smid & 255u], 1u) % (unsigned)kWarps);
+  }
+  double lnl = T.lnl0[j];
+  int n_acc = 0, n_like = 0;
+  int64_t n_bins = 0, n_spec = 0;
+  const double de_scale = 2.38 / sqrt(2.0 * (double)D);
+  const float de_scale32 = (float)de_scale;
+  __syncthreads();
+  const int sw = s_setup_warp;
+  int t = 0;
+  while (t < n_steps) {
+    const int W = min(window, n_steps - t);
+    // 1a. every thread screens one candidate step in FP32
+    int maybe = 0;
+    const int step = t + (int)threadIdx.x;
+    if ((int)threadIdx.x < W) {
+      Philox4 A = philox4x64((uint64_t)step, wid, it, 0ull, T.key0, T.key1);
+      uint64_t a = rand_index(A.v[0], n_s);
+      uint64_t b = rand_index(A.v[1], n_s - 1);
+      b += (b >= a) ? 1ull : 0ull;
+      float sc = 1.0f;
+      if ((A.v[2] >> 63) == 0ull) {
+        Philox4 B = philox4x64((uint64_t)step, wid, it, 1ull, T.key0, T.key1);
+        // log2 U_i = log2((x_i >> 12) + 1/2) - 52, each factor's integer rounded to float
+        // (relative error 6e-8, no truncation, no underflow of the product)
+        float l2 = __log2f(__ull2float_rn(B.v[0] >> 12) + 0.5f) + __log2f(__ull2float_rn(B.v[1] >> 12) + 0.5f) +
+                   __log2f(__ull2float_rn(B.v[2] >> 12) + 0.5f) + __log2f(__ull2float_rn(B.v[3] >> 12) + 0.5f) -
+                   208.0f;
+        sc = de_scale32 * (-0.25f * 0.6931471805599453f * l2);
+      }
+      // |x32 - x64| stays below ~1e-7 (1 + |s|) plus the log2 error times |s|: a margin of
+      // 1e-5 (1 + |s|) never rejects a step that the exact FP64 test accepts
+      const float margin = 1e-5f * (1.0f + fabsf(sc));
+      maybe = 1;
+      if (T.surv32) {
+        const float* ua = T.surv32 + a * D;
+        const float* ub = T.surv32 + b * D;
+#pragma unroll
+        for (int d = 0; d < kMaxDim; ++d) {
+          if (d < D && !ev.prior[ev.dim_param[d]].periodic) {
+            float x = u32[d] + sc * (ua[d] - ub[d]);
+            if (!(x >= -margin && x <= 1.0f + margin)) maybe = 0;
+          }
+        }
+      } else {
+        const double* ua = T.surv + a * D;
+        const double* ub = T.surv + b * D;
+#pragma unroll
+        for (int d = 0; d < kMaxDim; ++d) {
+          if (d < D && !ev.prior[ev.dim_param[d]].periodic) {
+            float x = u32[d] + sc * ((float)ua[d] - (float)ub[d]);
+            if (!(x >= -margin && x <= 1.0f + margin)) maybe = 0;
+          }
+        }
+      }
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, maybe);
+    if (lane == 0) wcount[warp] = __popc(mask);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < kWarps; ++w2) {
+      int cw = wcount[w2];
+      before += (w2 < warp) ? cw : 0;
+      total += cw;
+    }
+    const int mslot = before + __popc(mask & ((1u << lane) - 1u));
+    if (maybe && mslot < 32) mstep[mslot] = step;
+    const int nmaybe = min(total, 32);
+    __syncthreads();
+    // 1b. the setup warp redoes the maybe-in-bounds steps exactly (FP64, as the walk is
+    //     defined) and compacts the in-bounds ones into at most m slots
+    if (warp == sw) {
+      int in = 0;
+      double pr[kMaxDim];
+      const int st = lane < nmaybe ? mstep[lane] : 0;
+      if (lane < nmaybe) {
+        Philox4 A = philox4x64((uint64_t)st, wid, it, 0ull, T.key0, T.key1);
+        uint64_t a = rand_index(A.v[0], n_s);
+        uint64_t b = rand_index(A.v[1], n_s - 1);
+        b += (b >= a) ? 1ull : 0ull;
+        double sc;
+        if ((A.v[2] >> 63) == 1ull) {
+          sc = 1.0;
+        } else {
+          Philox4 B = philox4x64((uint64_t)st, wid, it, 1ull, T.key0, T.key1);
+          double prod = __dmul_rn(__dmul_rn(__dmul_rn(rand_open_unit(B.v[0]), rand_open_unit(B.v[1])),
+                                            rand_open_unit(B.v[2])), rand_open_unit(B.v[3]));
+          sc = __dmul_rn(de_scale, __dmul_rn(-0.25, log(prod)));
+        }
+        const double* ua = T.surv + a * D;
+        const double* ub = T.surv + b * D;
+        in = 1;
+#pragma unroll
+        for (int d = 0; d < kMaxDim; ++d) {
+          if (d < D) {
+            double x = __dadd_rn(u[d], __dmul_rn(sc, __dsub_rn(ua[d], ub[d])));
+            if (ev.prior[ev.dim_param[d]].periodic) x = __dsub_rn(x, floor(x));
+            // 0 <= x <= 1 on the bit pattern (integer pipe): +0 .. 1.0 are the patterns up
+            // to 0x3FF0000000000000; negative values and NaN compare above.  x is never -0.
+            if ((unsigned long long)__double_as_longlong(x) > 0x3FF0000000000000ull) in = 0;
+            pr[d] = x;
+          }
+        }
+      }
+      const unsigned im = __ballot_sync(0xffffffffu, in);
+      const int slot = __popc(im & ((1u << lane) - 1u));
+      if (in && slot < m) {
+#pragma unroll
+        for (int d = 0; d < kMaxDim; ++d)
+          if (d < D) prop[slot][d] = pr[d];
+        cstep[slot] = st;
+      }
+      const int nin_w = min(__popc(im), m);
+      // steps covered by this round: up to the m-th in-bounds proposal, else up to the last
+      // screened maybe-step, else the whole window
+      const unsigned mth = __ballot_sync(0xffffffffu, in && slot == m - 1);
+      int end;
+      if (__popc(im) > m) end = __shfl_sync(0xffffffffu, st, __ffs(mth) - 1);
+      else if (total > 32) end = __shfl_sync(0xffffffffu, st, 31);
+      else end = t + W - 1;
+      if (lane == 0) { s_nin = nin_w; s_end = end; }
+      __syncwarp();
+      if (lane < nin_w) setup_from_unit<PREC, WF>(ev, prop[lane], P[lane]);
+    }
+    __syncthreads();
+    const int nin = s_nin;
+    // 2. likelihoods
+    if (nin >= kWarps) {
+      // one warp per proposal; sums parked in shared memory, then one lane per proposal
+      // converts and assembles (the FP64 part runs once per proposal, on one warp)
+      for (int i = warp; i < nin; i += kWarps) {
+        double dv[NV];
+        float fv[NV], fc[NV];
+        partials<PREC, NDET, WF>(ev, P[i], lane, 32, dv, fv, fc);
+        if (PREC == 0) {
+          warp_reduce_f64<NV>(dv);
+          if (lane == 0) lnl_p[i] = lnl_from_vals<PREC, NDET, WF>(ev, P[i], dv);
+        } else {
+          warp_reduce_f32<NV>(fv, fc);
+          if (lane == 0)
+            for (int q = 0; q < NV; ++q) { part_sums[i][2 * q] = fv[q]; part_sums[i][2 * q + 1] = fc[q]; }
+        }
+      }
+      if (PREC != 0) {
+        __syncthreads();
+        if (warp == sw && lane < nin) {
+          double v[NV];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) v[q] = (double)part_sums[lane][2 * q] + (double)part_sums[lane][2 * q + 1];
+          lnl_p[lane] = lnl_from_vals<PREC, NDET, WF>(ev, P[lane], v);
+        }
+      }
+    } else {
+      for (int i = 0; i < nin; ++i) {
+        cta_sums<PREC, NDET, WF>(ev, P[i], red, vals);
+        if (threadIdx.x == 0) lnl_p[i] = lnl_from_vals<PREC, NDET, WF>(ev, P[i], vals);
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+    // 3. the steps in order
+    if (threadIdx.x == 0) {
+      int nxt = s_end + 1;
+      for (int i = 0; i < nin; ++i) {
+        ++n_like;
+        n_bins += P[i].k_end;
+        if (lnl_p[i] > lnl_star) {
+          for (int d = 0; d < D; ++d) { u[d] = prop[i][d]; u32[d] = (float)prop[i][d]; }
+          lnl = lnl_p[i];
+          ++n_acc;
+          nxt = cstep[i] + 1;
+          break;
+        }
+      }
+      n_spec += nin;
+      s_next = nxt;
+    }
+    __syncthreads();
+    t = s_next;
+  }
+  if (threadIdx.x < D) T.u_out[(size_t)j * D + threadIdx.x] = u[threadIdx.x];
+  if (threadIdx.x == 0) {
+    T.lnl_out[j] = lnl;
+    T.n_acc[j] = n_acc;
+    T.n_like[j] = n_like;
+    if (T.n_bins) T.n_bins[j] = n_bins;
+    if (T.n_spec) T.n_spec[j] = n_spec;
+  }
+}
+
+}  // namespace
+
+// Launchers of one precision P; each kernels_pP.cu instantiates its own.
+#define GWNS_DISPATCH_N(K, P, W)                                                  \
+  if (n_det == 1) K(P, 1, W); else if (n_det == 2) K(P, 2, W);                    \
+  else if (n_det == 3) K(P, 3, W); else K(P, 4, W);
+#define GWNS_DISPATCH_W(K, P)                                                     \
+  if (waveform == 0) { GWNS_DISPATCH_N(K, P, 0) } else { GWNS_DISPATCH_N(K, P, 1) }
+
+template <int P>
+cudaError_t launch_likelihood_p(int waveform, int n_det, const EventDev* d_ev, const double* d_theta, int n,
+                                double* d_lnl, int32_t* d_status, cudaStream_t s) {
+#define GWNS_LIK(P_, N, W) likelihood_kernel<P_, N, W><<<n, kThreads, 0, s>>>(d_ev, d_theta, n, d_lnl, d_status)
+  GWNS_DISPATCH_W(GWNS_LIK, P)
+#undef GWNS_LIK
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_unit_likelihood_p(int waveform, int n_det, const EventDev* d_ev, const double* d_u, int n,
+                                     double* d_lnl, cudaStream_t s) {
+#define GWNS_UL(P_, N, W) unit_likelihood_kernel<P_, N, W><<<n, kThreads, 0, s>>>(d_ev, d_u, n, d_lnl)
+  GWNS_DISPATCH_W(GWNS_UL, P)
+#undef GWNS_UL
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_walk_p(int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
+                          const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s) {
+#define GWNS_WALK(P_, N, W) \
+  walk_kernel<P_, N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local)
+  GWNS_DISPATCH_W(GWNS_WALK, P)
+#undef GWNS_WALK
+  return cudaGetLastError();
+}
+
+}  // namespace gwns

@@ -1,0 +1,30 @@
+// kernels_p0.cu -- kernels of precision 0 (FP64).
+#include "kernels_impl.cuh"
+
+namespace gwns {
+
+template cudaError_t launch_likelihood_p<0>(int, int, const EventDev*, const double*, int, double*, int32_t*,
+                                             cudaStream_t);
+template cudaError_t launch_unit_likelihood_p<0>(int, int, const EventDev*, const double*, int, double*,
+                                                  cudaStream_t);
+template cudaError_t launch_walk_p<0>(int, int, const EventDev*, WalkTask*, const int32_t*, const int32_t*, int,
+                                       cudaStream_t);
+
+cudaError_t launch_unit_to_theta(const EventDev* d_ev, const double* d_u, int64_t n, double* d_theta,
+                                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  unit_to_theta_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(d_ev, d_u, n, d_theta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_waveform(int waveform, int n_det, const EventDev* d_ev, const double* d_theta, int n, int n_bins,
+                            double* d_hre, double* d_him, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid((n_bins + 255) / 256, n);
+#define GWNS_WF(P_, N, W) waveform_kernel<N, W><<<grid, 256, 0, s>>>(d_ev, d_theta, n_bins, d_hre, d_him)
+  GWNS_DISPATCH_W(GWNS_WF, 0)
+#undef GWNS_WF
+  return cudaGetLastError();
+}
+
+}  // namespace gwns

@@ -407,7 +407,7 @@ int enqueue_batch(ns_handle* h, int b) {
   // flag makes it an event-record node that timestamps every replay
   if ((e = cudaEventRecordWithFlags(h->walk_events[2 * b], h->stream, cudaEventRecordExternal)) != cudaSuccess)
     return cuda_fail(h, e, "event");
-  e = launch_walk(h->precision, h->max_det, h->d_events, h->d_tasks, h->d_blk_task, h->d_blk_local,
+  e = launch_walk(h->precision, h->waveform, h->max_det, h->d_events, h->d_tasks, h->d_blk_task, h->d_blk_local,
                   h->n_walk_blocks, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "walk launch");
   if ((e = cudaEventRecordWithFlags(h->walk_events[2 * b + 1], h->stream, cudaEventRecordExternal)) != cudaSuccess)
@@ -523,7 +523,7 @@ int nested_init(ns_handle* h) {
   for (int e = 0; e < ne; ++e) {
     NsState& S = h->events[e].ns;
     init_live_kernel<<<(S.n_live + 127) / 128, 128, 0, h->stream>>>(h->d_ns, e);
-    if ((err = launch_unit_likelihood(h->precision, h->events[e].n_det, h->d_events + e, S.live_u, S.n_live,
+    if ((err = launch_unit_likelihood(h->precision, h->waveform, h->events[e].n_det, h->d_events + e, S.live_u, S.n_live,
                                       S.live_lnl, h->stream)) != cudaSuccess)
       return cuda_fail(h, err, "initial likelihoods");
     int64_t nl = S.n_live;

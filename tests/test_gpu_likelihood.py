@@ -26,7 +26,7 @@ def handle(w, ev, precision):
     return gwns.ns_init([cfg], [ev])
 
 
-@pytest.mark.parametrize("name", ["four_param_2det_taylorf2", "bbh11_3det_4s_taylorf2"])
+@pytest.mark.parametrize("name", ["four_param_2det_taylorf2", "bbh11_3det_4s_taylorf2", "bbh11_3det_8s_phenomd"])
 def test_waveform_elementwise(name):
     w, ev = event(name)
     h = handle(w, ev, synth.PREC_FP64)
@@ -55,6 +55,9 @@ def test_waveform_elementwise(name):
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED, TOL_MIXED),
     ("four_param_2det_taylorf2", synth.PREC_MIXED_FF, TOL_MIXED),
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, TOL_MIXED),
+    ("bbh11_3det_8s_phenomd", synth.PREC_FP64, TOL_FP64),
+    ("bbh11_3det_8s_phenomd", synth.PREC_MIXED, TOL_MIXED),
+    ("bbh11_3det_8s_phenomd", synth.PREC_MIXED_FF, TOL_MIXED),
 ])
 def test_likelihood_parity(name, precision, tol):
     w, ev = event(name)

@@ -46,10 +46,12 @@ def walk_inputs(w, ev, n_surv, n_walk, seed):
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED, 32),
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, 2),
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, 32),
+    ("bbh11_3det_8s_phenomd", synth.PREC_FP64, 8),
+    ("bbh11_3det_8s_phenomd", synth.PREC_MIXED_FF, 16),
 ])
 def test_walk_parity(name, precision, spec):
     # Any speculation depth gives the chain of the one-step-at-a-time walk.
-    w, ev = event(name)
+    w, ev = event(name, f_max=512.0) if "phenomd" in name else event(name)
     ll, surv, u0, l0, lnl_star = walk_inputs(w, ev, 60, 24, 4)
     n_steps, it, off = 12, 3, 7
     periodic = P.periodic_mask(priors(w, ev))
@@ -98,11 +100,12 @@ def test_walk_device_pointers_and_zero_steps():
         gwns.ns_free(h)
 
 
-@pytest.mark.parametrize("spec", [0, 1, 32])
-def test_batches_match_oracle_fp64(spec):
+@pytest.mark.parametrize("name,spec", [("four_param_2det_taylorf2", 0), ("four_param_2det_taylorf2", 1),
+                                       ("four_param_2det_taylorf2", 32), ("bbh11_3det_8s_phenomd", 0)])
+def test_batches_match_oracle_fp64(name, spec):
     # The whole batch pipeline (sort, deletion, evidence, starts, walk, insertion, retune)
     # on identical Philox streams: dead points and evidence agree after three batches.
-    w, ev = event("four_param_2det_taylorf2")
+    w, ev = event(name) if "four" in name else event(name, f_max=300.0, n_live=40)
     pri = priors(w, ev)
     ll = oracle_loglike(w, ev)
     batches = 3
