@@ -40,6 +40,10 @@ UNIT = "lnL evals/s"
 # its reduction (2); per detector the exact time-shift reduction (9), sincospi (20, its
 # polynomial), the complex multiply-accumulate (6) and two Kahan updates (8): 114 + 3 * 43.
 FP32_FLOPS_PER_WALKER_BIN = 243.0
+# IMRPhenomD form, merger-ringdown bins (most of the band): phase over 3 basis terms (42) plus
+# the atan term (~20) and reduction (2), amplitude shape (~12), per detector 43 + the template
+# power update (6): 76 + 3 * 49.
+FP32_FLOPS_PER_WALKER_BIN_PD = 223.0
 FP32_PEAK_TFLOPS = 80.5      # nominal GB300 FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz
 
 
@@ -82,6 +86,26 @@ def library_event(w: synth.Workload, seed_offset: int, device: int):
         d.data = hs[i] + (synth.gaussian_noise(psd, w.df, w.seed, 0, i) if w.noise else 0.0)
     ev.theta_inj = theta
     return w, ev
+
+
+def build_events(name: str, rank: int, device: int):
+    """Workloads and library-made events of a named bench workload."""
+    if name == "batched64":
+        ws = synth.batched_workloads(64, seed=100 + 1000 * rank)
+        out = [library_event(w, 0, device) for w in ws]
+        return [w for w, _ in out], [e for _, e in out]
+    w, ev = library_event(synth.workload(name), rank, device)
+    return [w], [ev]
+
+
+WORKLOAD_DESCRIPTIONS = {
+    "bbh11_3det_4s_taylorf2": "bbh11_3det_4s_taylorf2: 3 detectors, 4017 bins (4 s, 20-1024 Hz), TaylorF2, 11 params, "
+                              "n_live 1000, num_delete 500, naccept 60, SNR 39.6, seeded noise",
+    "bbh11_3det_8s_phenomd": "bbh11_3det_8s_phenomd: 3 detectors, 16,225 bins (8 s, 20-2048 Hz), IMRPhenomD form, "
+                             "11 params, n_live 2000, num_delete 1000, naccept 60, SNR 30, seeded noise",
+    "batched64": "batched64: 64 events in one handle, IMRPhenomD form, 3 detectors, 4/8/16 s "
+                 "(4017/16,225/32,449 bins), Mc U[10,60], SNR U[12,40], n_live U{500..2000}, num_delete n_live/2",
+}
 
 
 # ---------------------------------------------------------------- clocks
@@ -219,18 +243,27 @@ def run_ours(args):
         dist.all_reduce(t, op=op)
         return float(t.item())
 
-    w0 = synth.workload(WORKLOAD)
-    w, ev = library_event(w0, rank, local)
-    pri = synth.priors_with_injection(w, ev)
+    ws, evs = build_events(args.workload, rank, local)
+    w, ev = ws[0], evs[0]
+    ne = len(evs)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    def configs(precision):
+        return [gwns.make_config(wi, synth.priors_with_injection(wi, ei), precision=precision) for wi, ei in zip(ws, evs)]
+
+    def total(progress):
+        keys = ("n_like", "n_bins", "n_spec")
+        out = {k: sum(p[k] for p in progress) for k in keys}
+        out.update({k: progress[0][k] for k in ("walk_ms", "kernel_launches", "spec_depth", "n_steps", "mean_accept")})
+        return out
+
     def timed_steps(precision, steps, warmup, sample_clocks=False):
-        cfg = gwns.make_config(w, pri, precision=precision)
-        h = gwns.ns_init([cfg], [ev], local)
+        h = gwns.ns_init(configs(precision), evs, local)
         try:
             for _ in range(warmup):
-                gwns.ns_step(h, 1)
-            _, p0 = gwns.ns_step(h, 0)
+                gwns.ns_step(h, 1, ne)
+            _, p0 = gwns.ns_step(h, 0, ne)
+            p0 = [total(p0)]
             ms = 0.0
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             clocks = ClockSampler(local) if sample_clocks else None
@@ -243,7 +276,7 @@ def run_ours(args):
                 flush.zero_()                      # L2 flushed between steps (outside the events)
                 torch.cuda.synchronize()
                 e0.record()
-                _, p = gwns.ns_step(h, 1)          # synchronous: returns when the batch is done
+                _, p = gwns.ns_step(h, 1, ne)      # synchronous: returns when the batch is done
                 e1.record()
                 torch.cuda.synchronize()
                 ms += e0.elapsed_time(e1)
@@ -252,7 +285,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             barrier()
             wall = time.perf_counter() - wall0
-            p1 = p[0]
+            p1 = total(p)
             res = {"ms": ms, "wall_s": wall, "evals": p1["n_like"] - p0[0]["n_like"],
                    "bins": p1["n_bins"] - p0[0]["n_bins"], "walk_ms": p1["walk_ms"] - p0[0]["walk_ms"],
                    "spec": p1["n_spec"] - p0[0]["n_spec"],
@@ -277,27 +310,28 @@ def run_ours(args):
 
     # end to end through the public API with host buffers: init (host data upload and the
     # initial live points), K batches, evidence read back
-    cfg = gwns.make_config(w, pri, precision=synth.PREC_MIXED_FF)
-    keep_ev = gwns.make_event(ev)
+    cfgs = configs(synth.PREC_MIXED_FF)
+    keep = [gwns.make_event(e) for e in evs]
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    h = gwns.ns_init([cfg], [keep_ev[0]], local)
+    h = gwns.ns_init(cfgs, [k[0] for k in keep], local)
     try:
         for _ in range(args.steps):
-            gwns.ns_step(h, 1)
-        lz, lz_err, info, n_like_e2e = gwns.ns_evidence(h, 0)
-        _, pe = gwns.ns_step(h, 0)
+            gwns.ns_step(h, 1, ne)
+        evid = [gwns.ns_evidence(h, e) for e in range(ne)]
+        _, pe = gwns.ns_step(h, 0, ne)
     finally:
         gwns.ns_free(h)
     e1.record()
     torch.cuda.synchronize()
+    lz, lz_err = evid[0][0], evid[0][1]
     e2e_ms = reduce(e0.elapsed_time(e1), dist.ReduceOp.MAX if dist else None)
-    e2e_evals = reduce(float(n_like_e2e), dist.ReduceOp.SUM if dist else None)
-    h2d = len(ev.detectors) * ev.n_bins * 3 * 8 / args.steps
-    n_dead = pe[0]["iterations"] * w.num_delete
-    d2h = 288 + (2 * n_dead * 8 + w.n_live * 8 + 200 * 8) / args.steps
+    e2e_evals = reduce(float(sum(x[3] for x in evid)), dist.ReduceOp.SUM if dist else None)
+    h2d = sum(len(e.detectors) * e.n_bins * 3 * 8 for e in evs) / args.steps
+    d2h = (288 * ne + sum(2 * p["iterations"] * wi.num_delete * 8 + wi.n_live * 8 + 200 * 8
+                          for p, wi in zip(pe, ws))) / args.steps
 
     if rank != 0:
         if dist is not None:
@@ -309,18 +343,19 @@ def run_ours(args):
     walk_launches = args.steps
     walk_ms_avg = mixed["walk_ms"] / walk_launches
     bins_evaluated = mixed["bins"] * mixed["spec"] / max(mixed["evals"], 1)
-    achieved = bins_evaluated * FP32_FLOPS_PER_WALKER_BIN / (mixed["walk_ms"] * 1e-3) / 1e12
+    achieved = bins_evaluated * (FP32_FLOPS_PER_WALKER_BIN if w.waveform == synth.TAYLORF2
+                                 else FP32_FLOPS_PER_WALKER_BIN_PD) / (mixed["walk_ms"] * 1e-3) / 1e12
     cpu_rate, cpu_info = oracle_walk_rate(w, ev, budget_s=args.cpu_seconds)
+    fp32_flops = FP32_FLOPS_PER_WALKER_BIN if w.waveform == synth.TAYLORF2 else FP32_FLOPS_PER_WALKER_BIN_PD
     clocks = mixed["clocks"] or {}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: 3 detectors, 4017 bins (4 s, 20-1024 Hz), TaylorF2, 11 params, "
-                               f"n_live 1000, num_delete 500, naccept 60, SNR 39.6, seeded noise",
+        "config": {"workload": WORKLOAD_DESCRIPTIONS[args.workload],
                    "precision": "mixed: FP32 sums, float-float phase, FP64 per-walker constants and lnL assembly",
                    "step": "one sampler batch (select, walk, insert)",
-                   "l2": "flushed (256 MB write) between timed steps", "events_per_rank": 1},
+                   "l2": "flushed (256 MB write) between timed steps", "events_per_rank": ne},
         "plain_fp64": {"value": value_plain, "unit": UNIT, "ms_per_step": t_plain / args.steps},
         "mixed_fp64_phase": {"value": value_m64, "unit": UNIT, "ms_per_step": t_m64 / args.steps},
         "mixed_over_plain": value / value_plain,
@@ -331,7 +366,8 @@ def run_ours(args):
         "e2e": {"value": e2e_evals / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": args.steps, "log_z": lz, "log_z_err": lz_err},
         "gpu_launches": int(mixed["launches"]),
-        "roofline": {"bound": "alu", "pipe": "fp32", "kernel": "walk_kernel<2,3> (float-float phase)",
+        "roofline": {"bound": "alu", "pipe": "fp32",
+                     "kernel": f"walk_kernel<2,3,{w.waveform}> (float-float phase)",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "avg_launch_ms": walk_ms_avg,
@@ -355,12 +391,12 @@ def run_profile_case(args):
     build.build()
     gwns.load()
     torch.cuda.set_device(0)
-    w, ev = library_event(synth.workload(WORKLOAD), 0, 0)
-    pri = synth.priors_with_injection(w, ev)
-    h = gwns.ns_init([gwns.make_config(w, pri, precision=args.precision)], [ev])
+    ws, evs = build_events(args.workload, 0, 0)
+    cfgs = [gwns.make_config(w, synth.priors_with_injection(w, e), precision=args.precision) for w, e in zip(ws, evs)]
+    h = gwns.ns_init(cfgs, evs)
     try:
         for _ in range(args.profile_batches):
-            _, p = gwns.ns_step(h, 1)
+            _, p = gwns.ns_step(h, 1, len(evs))
         print(json.dumps(p[0]))
     finally:
         gwns.ns_free(h)
@@ -377,6 +413,8 @@ def main():
     ap.add_argument("--profile-batches", type=int, default=0,
                     help="run this many batches of the workload without timing (a small case for ncu)")
     ap.add_argument("--precision", type=int, default=synth.PREC_MIXED_FF)
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCRIPTIONS),
+                    help="bench workload (the default is the headline line)")
     args = ap.parse_args()
     if args.profile_batches > 0:
         return run_profile_case(args)

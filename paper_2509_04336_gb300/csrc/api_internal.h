@@ -23,7 +23,7 @@ struct NsState {
   double log_x, log_z, lnl_star, dlogz, mean_accept, lnl_max, delay_k, term_value;
   int64_t n_dead, n_like, iteration, max_iter, dead_cap, n_bins_eval, n_spec_eval;
   int32_t n_live, k, D, n_steps, naccept, maxmcmc, term_kind, done, zero_accept, overflow;
-  int32_t spec, spec_auto, spec_cap, pad;
+  int32_t spec, spec_auto, spec_cap, spec_rule;   // spec = min(spec_rule, spec_cap)
   uint64_t key0, key1;
   double* live_u;      // [n_live][D]
   double* live_lnl;    // [n_live]
@@ -76,11 +76,16 @@ struct ns_handle {
   int32_t* d_blk_task = nullptr;
   int32_t* d_blk_local = nullptr;
   int n_walk_blocks = 0;
-  cudaGraphExec_t graph_exec = nullptr;
-  int graph_batches = 0;
+  cudaGraphExec_t graph_exec[9] = {};   // instantiated batch graphs, indexed by batches per replay
   std::vector<cudaEvent_t> walk_events;  // [2 * batches in the graph]: start, end of each walk
   double walk_ms = 0.0;
   int64_t kernel_launches = 0;
+  // speculation-depth autotuner (all events in automatic mode)
+  bool tune = false;
+  int tune_next = 3;                 // iteration at which the next tuning pass starts
+  int tune_idx = -1;                 // candidate under trial, -1 when not tuning
+  double tune_cost[8] = {0};
+  int tune_best = 32;
   std::vector<gwns::NsState> host_ns;   // last progress snapshot
   std::string err;
 };

@@ -238,8 +238,9 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
     // falls on average about halfway through a round
     if (S.spec_auto) {
       double p = mean_acc / fmax(tot_calls / (double)k, 1.0);
-      double m = p > 0.0 ? floor(0.7 / p + 0.5) : (double)S.spec_cap;
-      S.spec = (int32_t)fmin(fmax(m, 1.0), (double)S.spec_cap);
+      double m = p > 0.0 ? floor(0.7 / p + 0.5) : (double)kSpecMax;
+      S.spec_rule = (int32_t)fmin(fmax(m, 1.0), (double)kSpecMax);
+      S.spec = min(S.spec_rule, S.spec_cap);
     }
     if (n_zero > 0.0) S.zero_accept = 1;
     // walk-length retune (batch-scaled delay)
@@ -418,11 +419,10 @@ int enqueue_batch(ns_handle* h, int b) {
 }
 
 int build_graph(ns_handle* h, int batches) {
-  if (h->graph_exec && h->graph_batches == batches) return NS_OK;
-  if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+  if (h->graph_exec[batches]) return NS_OK;
   cudaGraph_t g;
   cudaError_t e;
-  while ((int)h->walk_events.size() < 2 * batches) {
+  while ((int)h->walk_events.size() < 2 * 8) {
     cudaEvent_t ev;
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(h, e, "event create");
     h->walk_events.push_back(ev);
@@ -435,10 +435,9 @@ int build_graph(ns_handle* h, int batches) {
   }
   e = cudaStreamEndCapture(h->stream, &g);
   if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
-  e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+  e = cudaGraphInstantiate(&h->graph_exec[batches], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
-  h->graph_batches = batches;
   return NS_OK;
 }
 
@@ -475,6 +474,7 @@ int nested_init(ns_handle* h) {
     S.dead_cap = (int64_t)S.k * 64;
     S.spec_auto = c.spec_depth == 0;
     S.spec_cap = h->precision == 0 ? 8 : kSpecMax;
+    S.spec_rule = 4;
     S.spec = c.spec_depth > 0 ? c.spec_depth : 4;
     const size_t n = S.n_live, k = S.k, D = S.D;
     if ((r = alloc(h, (void**)&S.live_u, sizeof(double) * n * D, "live_u")) ||
@@ -534,7 +534,7 @@ int nested_init(ns_handle* h) {
 }
 
 void nested_free(ns_handle* h) {
-  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  for (auto& g : h->graph_exec) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   for (cudaEvent_t ev : h->walk_events) cudaEventDestroy(ev);
   h->walk_events.clear();
   for (auto& E : h->events) {
@@ -573,6 +573,28 @@ static void fill_progress(ns_handle* h, ns_progress* p) {
   }
 }
 
+namespace {
+// Candidate caps of the speculation depth tried by the autotuner.
+const int kTuneCaps[] = {2, 4, 8, 16, 32};
+const int kTuneCapsF64[] = {1, 2, 4, 8};
+
+// Sets the speculation cap of every event, and the depth of the next walk to the rule
+// value under that cap.
+int set_spec_cap(ns_handle* h, int cap) {
+  for (size_t e = 0; e < h->events.size(); ++e) {
+    const NsState& S = h->host_ns[e];
+    int32_t spec = S.spec_rule < cap ? S.spec_rule : cap;
+    NsState* d = h->d_ns + e;
+    cudaError_t err;
+    if ((err = cudaMemcpy(&d->spec_cap, &cap, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+        (err = cudaMemcpy(&d->spec, &spec, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+        (err = cudaMemcpy(&h->d_tasks[e].spec, &spec, sizeof(int32_t), cudaMemcpyHostToDevice)))
+      return cuda_fail(h, err, "speculation cap");
+  }
+  return NS_OK;
+}
+}  // namespace
+
 extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
   if (!h) return set_error(nullptr, NS_EINVAL, "handle is NULL");
   if (max_batches < 0) return set_error(h, NS_EINVAL, "max_batches < 0");
@@ -583,11 +605,30 @@ extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
   for (auto& S : h->host_ns) all_done = all_done && S.done;
   int left = all_done ? 0 : max_batches;
   const int G = 8;
+  bool all_auto = true;
+  for (auto& E : h->events) all_auto = all_auto && E.ns.spec_auto;
+  h->tune = all_auto;
+  const int* caps = h->precision == 0 ? kTuneCapsF64 : kTuneCaps;
+  const int n_caps = h->precision == 0 ? 4 : 5;
   while (left > 0) {
     int b = left < G ? left : G;
+    // Autotuning of the speculation cap: from iteration tune_next, one batch per candidate,
+    // scored by walk-kernel device time per likelihood call; the best cap is kept until the
+    // next pass 32 iterations later.  Any depth gives the same chain, so this only moves time.
+    int64_t it_now = h->host_ns.empty() ? 0 : h->host_ns[0].iteration;
+    int64_t like0 = 0;
+    double ms0 = h->walk_ms;
+    bool trial = false;
+    if (h->tune && (h->tune_idx >= 0 || it_now >= h->tune_next)) {
+      if (h->tune_idx < 0) h->tune_idx = 0;
+      if ((r = set_spec_cap(h, caps[h->tune_idx]))) return r;
+      for (auto& S : h->host_ns) like0 += S.n_like;
+      b = 1;
+      trial = true;
+    }
     if ((r = ensure_dead_capacity(h, b))) return r;
     if ((r = build_graph(h, b))) return r;
-    cudaError_t e = cudaGraphLaunch(h->graph_exec, h->stream);
+    cudaError_t e = cudaGraphLaunch(h->graph_exec[b], h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
     if ((r = download_states(h))) return r;
     for (int i = 0; i < b; ++i) {
@@ -597,6 +638,19 @@ extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
       h->walk_ms += ms;
     }
     h->kernel_launches += 3 * (int64_t)b;
+    if (trial) {
+      int64_t like1 = 0;
+      for (auto& S : h->host_ns) like1 += S.n_like;
+      h->tune_cost[h->tune_idx] = (h->walk_ms - ms0) / (double)(like1 > like0 ? like1 - like0 : 1);
+      if (++h->tune_idx == n_caps) {
+        int best = 0;
+        for (int i = 1; i < n_caps; ++i) if (h->tune_cost[i] < h->tune_cost[best]) best = i;
+        h->tune_best = caps[best];
+        if ((r = set_spec_cap(h, h->tune_best))) return r;
+        h->tune_idx = -1;
+        h->tune_next = (int)h->host_ns[0].iteration + 32;
+      }
+    }
     left -= b;
     all_done = true;
     for (auto& S : h->host_ns) all_done = all_done && S.done;

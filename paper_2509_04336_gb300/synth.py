@@ -278,3 +278,41 @@ def priors_with_injection(w: Workload, ev: Event) -> list:
     for i, p in enumerate(w.priors):
         out.append(replace(p, value=float(ev.theta_inj[i])) if p.kind == FIXED else p)
     return out
+
+
+def batched_workloads(n_events: int = 64, seed: int = 100, waveform: int = PHENOMD_FORM,
+                      precision: int = PREC_MIXED_FF) -> list:
+    """Seeded population of independent events sampled together in one launch.
+
+    Event e: Mc ~ U[10, 60] Msun, q ~ U[0.25, 1], spins ~ U[-0.8, 0.8], the other parameters
+    from the Table 1 priors; target network SNR ~ U[12, 40]; duration 4, 8 or 16 s, the
+    smallest exceeding the Newtonian chirp time from 20 Hz plus 2 s, except that the first
+    three quarters of the events are stratified over the three durations so that each
+    appears at least n_events/4 times (20-1024 Hz at 4 s, 20-2048 Hz at 8 and 16 s: 4017,
+    16,225 and 32,449 bins); n_live ~ U{500, 600, ..., 2000}, num_delete = n_live / 2;
+    priors Mc +- 25 % around the injection, q [0.25, 1], spins [-0.8, 0.8]; noise seed 100 + e.
+    """
+    rng = np.random.Generator(np.random.Philox(key=np.array([seed, 4444], dtype=np.uint64)))
+    out = []
+    tsun = 4.925490947641267e-06
+    for e in range(n_events):
+        mc = rng.uniform(10.0, 60.0)
+        q = rng.uniform(0.25, 1.0)
+        chi = rng.uniform(-0.8, 0.8, size=2)
+        u = rng.random(7)
+        inj = np.array([mc, q, chi[0], chi[1], 1000.0, math.acos(1 - 2 * u[0]), math.pi * u[1],
+                        2 * math.pi * u[2], -0.1 + 0.2 * u[3], 2 * math.pi * u[4], math.asin(2 * u[5] - 1)])
+        snr = rng.uniform(12.0, 40.0)
+        # Newtonian chirp time from 20 Hz (seconds)
+        tau0 = 5.0 / 256.0 * (math.pi * 20.0) ** (-8.0 / 3.0) * (mc * tsun) ** (-5.0 / 3.0)
+        natural = next((d for d in (4.0, 8.0, 16.0) if d > tau0 + 2.0), 16.0)
+        strata = (4.0, 8.0, 16.0)
+        duration = strata[e % 3] if e < (3 * n_events) // 4 else natural
+        f_max = 1024.0 if duration == 4.0 else 2048.0
+        n_live = int(rng.integers(5, 21)) * 100
+        pri = _standard_priors((0.75 * mc, 1.25 * mc), (0.25, 1.0), (-0.8, 0.8))
+        w = Workload(f"batched_{e}", ("H", "L", "V"), 20.0, f_max, duration, waveform, inj, snr, True, pri,
+                     n_live=n_live, num_delete=n_live // 2, naccept=60, maxmcmc=5000,
+                     term_kind=TERM_DLOGZ, term_value=0.1, seed=100 + e, precision=precision)
+        out.append(w)
+    return out

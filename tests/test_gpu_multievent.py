@@ -1,0 +1,66 @@
+"""Several independent events sampled in one handle (one walk grid over all their walkers,
+uneven bin counts, live counts and walk lengths): every event follows its own oracle run."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from oracle import likelihood as L, nested, prior as P
+from paper_2509_04336_gb300 import gwns, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2509_04336_gb300 import build
+    build.build()
+
+
+def small_events(precision):
+    ws = synth.batched_workloads(8, seed=7, precision=precision)
+    picks = [ws[0], ws[1], ws[2], ws[5]]
+    out = []
+    for i, w in enumerate(picks):
+        n_live = (30, 44, 36, 50)[i]
+        w = replace(w, f_max=w.f_min + 40.0, n_live=n_live, num_delete=n_live // 2, naccept=6, maxmcmc=200)
+        ev = synth.make_event(w, lambda e, d, th, ww=w: L.project(e, d, th, ww.waveform), L.inner)
+        out.append((w, ev))
+    return out
+
+
+def test_events_in_one_handle_follow_their_oracle_runs():
+    evs = small_events(synth.PREC_FP64)
+    assert len({ev.n_bins for _, ev in evs}) >= 2
+    batches = 3
+    cfgs = [gwns.make_config(w, synth.priors_with_injection(w, ev), max_iter=batches) for w, ev in evs]
+    h = gwns.ns_init(cfgs, [ev for _, ev in evs])
+    try:
+        code, prog = gwns.ns_step(h, batches + 2, n_events=len(evs))
+        for e, (w, ev) in enumerate(evs):
+            pri = synth.priors_with_injection(w, ev)
+            ll = lambda u, ev=ev, pri=pri, w=w: L.log_likelihood(ev, P.transform(u, pri), w.waveform)
+            ref = nested.run_nested(ll, w.n_dim, w.n_live, w.num_delete, w.naccept, w.maxmcmc,
+                                    P.periodic_mask(pri), (w.seed, e), max_iter=batches, n_replay=2)
+            assert prog[e]["iterations"] == batches and prog[e]["done"] == 1
+            assert prog[e]["n_like"] == ref.n_like
+            assert abs(prog[e]["log_z"] - np.logaddexp.reduce(ref.dead_logw)) < 1e-9
+            th, lw = gwns.ns_posterior(h, e)
+            dead = np.stack([P.transform(u, pri) for u in ref.dead_u])
+            assert np.allclose(th[:dead.shape[0]], dead, rtol=1e-12, atol=1e-12)
+    finally:
+        gwns.ns_free(h)
+
+
+def test_mixed_precision_events_run_to_termination():
+    evs = small_events(synth.PREC_MIXED_FF)
+    cfgs = [gwns.make_config(w, synth.priors_with_injection(w, ev), max_iter=60) for w, ev in evs]
+    h = gwns.ns_init(cfgs, [ev for _, ev in evs])
+    try:
+        code, prog = gwns.ns_step(h, 60, n_events=len(evs))
+        for e, p in enumerate(prog):
+            assert p["done"] == 1 and np.isfinite(p["log_z"])
+            lz, err, info, n_like = gwns.ns_evidence(h, e)
+            assert np.isfinite(lz) and err > 0 and info > 0 and n_like == p["n_like"]
+    finally:
+        gwns.ns_free(h)
