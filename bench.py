@@ -45,6 +45,10 @@ FP32_FLOPS_PER_WALKER_BIN = 243.0
 # power update (6): 76 + 3 * 49.
 FP32_FLOPS_PER_WALKER_BIN_PD = 223.0
 FP32_PEAK_TFLOPS = 80.5      # nominal GB300 FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz
+# DRAM bytes (read + write) of one walk launch, from one ncu capture of this build's kernel
+# (walk_kernel<2, 3, WF>, batch 10 of the 4 s TaylorF2 workload and batch 3 of the 8 s
+# IMRPhenomD one); None for workloads without a capture.
+NCU_WALK_TRAFFIC_BYTES = {"bbh11_3det_4s_taylorf2": 337664 + 16384, "bbh11_3det_8s_phenomd": 8672256 + 885504}
 
 
 def rank_info():
@@ -369,7 +373,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "pipe": "fp32",
                      "kernel": f"walk_kernel<2,3,{w.waveform}> (float-float phase)",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": NCU_WALK_TRAFFIC_BYTES.get(args.workload),
                      "avg_launch_ms": walk_ms_avg,
                      "peak_source": "nominal GB300 FP32, 152 SMs x 128 lanes x 2 flop x 2.07 GHz; "
                                     "FMA microbenchmark measured 74.7"},
