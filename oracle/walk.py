@@ -12,12 +12,21 @@ Each of the W walkers runs n_steps steps in the unit hypercube.  At step t walke
   4. accepts iff ln L(u') > ln L*  (strict; ties reject).
 The Philox key is (seed, event).  Returns the final positions, their ln L, the
 accepted-step counts and the number of likelihood calls of each walker.
+
+Flow steps (survey rows a11/a12; the paper only motivates flows, Sec. 6): with a flow q
+(oracle.flow) and probability p_flow, step t is instead an independence proposal
+u' = F^-1(x), x ~ N(0, I) (oracle.flow.base_normals, flow_step_draws).  It is accepted iff
+ln U < ln q(u) - ln q(u') and ln L(u') > ln L*, a Metropolis-Hastings step for the uniform
+prior restricted to L > L*.  The q-ratio test is taken first, so a rejected ratio costs no
+likelihood call; ln q of the current point is carried along (re-evaluated after an
+accepted DE move).
 """
 import math
 
 import numpy as np
 
 from .philox import philox4x64_vec, mulhi_vec, open_unit_vec
+from . import flow as flowmod
 
 DE_SCALE = 2.38
 
@@ -38,8 +47,10 @@ def de_step_draws(t: int, walkers: np.ndarray, it: int, n_surv: int, n_dim: int,
 
 
 def acceptance_walk(loglike, u0, lnl0, lnl_star, survivors, n_steps, periodic, key, it,
-                    walker_ids=None):
-    """Run the walk for every walker.  loglike(u [D]) -> float; survivors [n_s, D]."""
+                    walker_ids=None, flow=None, p_flow=0.0, flow_bf16=False):
+    """Run the walk for every walker.  loglike(u [D]) -> float; survivors [n_s, D].
+    The returned margin is, per walker, the smallest distance of any accept decision from
+    its threshold: |ln L(u') - ln L*| and, on flow steps, |ln U - (ln q(u) - ln q(u'))|."""
     u = np.array(u0, dtype=np.float64, copy=True)
     lnl = np.array(lnl0, dtype=np.float64, copy=True)
     W, D = u.shape
@@ -49,15 +60,27 @@ def acceptance_walk(loglike, u0, lnl0, lnl_star, survivors, n_steps, periodic, k
     ids = np.arange(W) if walker_ids is None else np.asarray(walker_ids)
     n_acc = np.zeros(W, dtype=np.int64)
     n_like = np.zeros(W, dtype=np.int64)
-    margin = np.full(W, np.inf)   # smallest |ln L(u') - ln L*| met by each walker
+    margin = np.full(W, np.inf)   # smallest distance of a decision from its threshold
+    use_flow = flow is not None and p_flow > 0.0
+    if use_flow:
+        _, logq = flowmod.forward(flow, u, flow_bf16)
     for t in range(n_steps):
         a, b, s = de_step_draws(t, ids, it, n_s, D, key)
         prop = u + s[:, None] * (survivors[a] - survivors[b])
         prop = np.where(periodic[None, :], prop - np.floor(prop), prop)
+        if use_flow:
+            fstep, log_u = flowmod.flow_step_draws(t, ids, it, p_flow, key)
+            fu, fq = flowmod.inverse(flow, flowmod.base_normals(t, ids, it, D, key), flow_bf16)
+            prop = np.where(fstep[:, None], fu, prop)
         inside = np.all((prop >= 0.0) & (prop <= 1.0), axis=1)
         for w in range(W):
             if not inside[w]:
                 continue
+            if use_flow and fstep[w]:
+                ratio = logq[w] - fq[w]
+                margin[w] = min(margin[w], abs(log_u[w] - ratio))
+                if not log_u[w] < ratio:
+                    continue
             val = loglike(prop[w])
             n_like[w] += 1
             margin[w] = min(margin[w], abs(val - lnl_star))
@@ -65,4 +88,6 @@ def acceptance_walk(loglike, u0, lnl0, lnl_star, survivors, n_steps, periodic, k
                 u[w] = prop[w]
                 lnl[w] = val
                 n_acc[w] += 1
+                if use_flow:
+                    logq[w] = fq[w] if fstep[w] else flowmod.forward(flow, prop[w:w + 1], flow_bf16)[1][0]
     return u, lnl, n_acc, n_like, margin
