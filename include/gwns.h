@@ -79,6 +79,9 @@ extern "C" {
 #define NS_TERM_DLOGZ 0           /* stop when ln(Z + L_max X) - ln Z < term_value (Sec. 4.1.1)   */
 #define NS_TERM_FRAC_REMAINING 1  /* stop when L_mean X < term_value * Z (Sec. 4.2)              */
 
+#define NS_PROPOSAL_DE 0        /* differential-evolution steps only (Sec. 3.1)            */
+#define NS_PROPOSAL_DE_FLOW 1   /* DE steps mixed with flow independence proposals          */
+
 #define NS_PTR_HOST 0
 #define NS_PTR_DEVICE 1
 
@@ -110,7 +113,15 @@ typedef struct ns_config {
     uint64_t seed;        /* Philox key word 0; key word 1 is the event index      */
     int32_t spec_depth;   /* walk steps evaluated per round (1..32); 0: chosen per batch
                              from the acceptance rate.  Any value gives the same chain.  */
+    int32_t proposal;     /* NS_PROPOSAL_DE, or NS_PROPOSAL_DE_FLOW: DE steps mixed with
+                             independence proposals from a normalising flow trained on the
+                             live points (see "Flow proposal" below)                  */
+    double p_flow;        /* DE_FLOW: probability that a walk step is a flow step, [0, 1] */
+    int32_t flow_layers;  /* DE_FLOW: affine coupling layers, 1..16 (0: 8)            */
+    int32_t flow_every;   /* DE_FLOW: retrain the flow every this many batches (0: 1)  */
+    int32_t flow_epochs;  /* DE_FLOW: full-batch Adam steps per retraining (0: 20)     */
     int32_t reserved;     /* must be 0                                              */
+    double flow_lr;       /* DE_FLOW: Adam learning rate (0: 1e-3)                  */
 } ns_config;
 
 /* One detector's data.  Pointers are HOST arrays of n_bins doubles, copied by ns_init. */
@@ -227,6 +238,44 @@ int ns_posterior(ns_handle* h, int event, double* theta_out, double* logw_out,
  * same Philox streams and so replays bit-identically. */
 int ns_state_save(ns_handle* h, const char* path);
 int ns_state_load(ns_handle* h, const char* path);
+
+/* ---------------------------------------------------------------- Flow proposal
+ * The paper (Sec. 6) motivates normalising-flow proposals for a batched GPU nested sampler
+ * without fixing a design; this library's reading (an event configured with
+ * NS_PROPOSAL_DE_FLOW):
+ *   q(u) on the unit cube: z0 = (logit(u) - mu) / sigma, then L RealNVP affine coupling
+ *   layers (Dinh et al. 2017), layer l conditioning on the dimensions d with (d + l) even
+ *   through a tanh MLP D -> 128 -> 128 -> 2 D that gives log-scales s = 2 tanh(s_raw / 2)
+ *   and shifts t; base density N(0, I).  Matrix products run on the tensor cores with
+ *   bf16 operands and FP32 accumulation.
+ *   Walk: step t of walker w is a flow step with probability p_flow (Philox word
+ *   (t, walker_offset + w, iteration, 6)[0]); it proposes u' = F^-1(x), x ~ N(0, I) from
+ *   Philox blocks (t, walker_offset + w, iteration, 16 + c), and accepts iff
+ *   ln U < ln q(u) - ln q(u') (word 1) and ln L(u') > ln L* -- a Metropolis-Hastings step
+ *   that keeps the prior restricted to L > L* invariant.  The q test comes first, so a
+ *   rejected flow step costs no likelihood call.
+ *   Training: maximum likelihood on the n_live current points at the start of every
+ *   flow_every-th batch (mu, sigma re-estimated; flow_epochs full-batch Adam steps,
+ *   beta (0.9, 0.999), eps 1e-8; weights and Adam state carry over).
+ * Parameters are a flat FP32 vector, per layer W1 [128][D], b1 [128], W2 [128][128],
+ * b2 [128], W3 [2D][128] (rows: s_0..s_{D-1}, t_0..t_{D-1}), b3 [2D]; ns_flow_num_params
+ * gives its length.  Every call below returns NS_ESTATE for an event without a flow.
+ * Host pointers unless a ptr_kind says otherwise. */
+int ns_flow_num_params(ns_handle* h, int event, int32_t* n_params);
+/* Replace the flow's weights and standardisation (mu, sigma [D]); resets Adam. */
+int ns_flow_set(ns_handle* h, int event, const float* params, const double* mu, const double* sigma);
+int ns_flow_get(ns_handle* h, int event, float* params, double* mu, double* sigma);
+/* ln q(u) of n points u [n][D] strictly inside the unit cube. */
+int ns_flow_logq(ns_handle* h, int event, const double* u, int n, double* logq, int ptr_kind, void* stream);
+/* The proposal table a walk batch would use: for walkers w < n (walker ids walker_offset + w)
+ * and steps t < n_steps, u_out [n][n_steps][D] = F^-1(x) and logq_out [n][n_steps] = ln q. */
+int ns_flow_sample(ns_handle* h, int event, int64_t iteration, int64_t walker_offset, int n, int n_steps,
+                   double* u_out, double* logq_out, int ptr_kind, void* stream);
+/* Mean of -ln q over n points u [n][D] and its gradient grad [n_params] (no update). */
+int ns_flow_grad(ns_handle* h, int event, const double* u, int n, float* grad, double* loss);
+/* Re-estimate mu, sigma on u [n][D] (n <= 4096) and take `epochs` Adam steps on the mean of
+ * -ln q; losses [epochs] (may be NULL) receives the loss before each step. */
+int ns_flow_train(ns_handle* h, int event, const double* u, int n, int epochs, double* losses);
 
 void ns_free(ns_handle* h);
 const char* ns_last_error(ns_handle* h);

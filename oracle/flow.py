@@ -18,8 +18,9 @@ reading, kept deliberately plain:
       log q(u) = log N(x) + sum_l sum(s_l) - sum_d log sigma_d - sum_d log(u_d (1 - u_d));
 * inverse (sampling): z_{l-1} = m_l z_l + (1 - m_l)(z_l - t) exp(-s), u = sigmoid(sigma z_0 + mu);
 * loss = mean over the training points of -log q(u), minimised by Adam (Kingma & Ba 2015,
-  beta = (0.9, 0.999), eps = 1e-8, bias-corrected), full batch; a step with a non-finite
-  gradient is skipped;
+  beta = (0.9, 0.999), eps = 1e-8, bias-corrected), full batch; the step counter advances
+  every step, and a gradient component that is not finite leaves its parameter and moments
+  unchanged;
 * initial weights: W1 and W2 uniform on (-1, 1) / sqrt(fan_in) from Philox block
   (l, mat, e // 4, 5), word e % 4 (mat 0 = W1, 1 = W2; e the row-major element index);
   W3 and every bias start at zero, so the initial flow is the identity.
@@ -241,15 +242,17 @@ class Adam:
         self.lr = lr
 
     def step(self, params, grad):
-        """Returns the updated parameters; a non-finite gradient leaves everything unchanged."""
-        if not np.all(np.isfinite(grad)):
-            return params
+        """Returns the updated parameters; non-finite gradient components are skipped."""
         self.t += 1
-        self.m = ADAM_B1 * self.m + (1.0 - ADAM_B1) * grad
-        self.v = ADAM_B2 * self.v + (1.0 - ADAM_B2) * grad * grad
+        ok = np.isfinite(grad)
+        g = np.where(ok, grad, 0.0)
+        m = ADAM_B1 * self.m + (1.0 - ADAM_B1) * g
+        v = ADAM_B2 * self.v + (1.0 - ADAM_B2) * g * g
+        self.m = np.where(ok, m, self.m)
+        self.v = np.where(ok, v, self.v)
         mh = self.m / (1.0 - ADAM_B1 ** self.t)
         vh = self.v / (1.0 - ADAM_B2 ** self.t)
-        return params - self.lr * mh / (np.sqrt(vh) + ADAM_EPS)
+        return np.where(ok, params - self.lr * mh / (np.sqrt(vh) + ADAM_EPS), params)
 
 
 def train(flow: Flow, u, epochs: int, adam: Adam, bf16: bool = False, restandardise: bool = True):

@@ -81,7 +81,7 @@ static int check_config(const ns_config& c, int e) {
   if (c.term_kind != NS_TERM_DLOGZ && c.term_kind != NS_TERM_FRAC_REMAINING)
     return set_error(nullptr, NS_EINVAL, "event %d: unknown termination %d", e, c.term_kind);
   if (!(c.term_value > 0.0)) return set_error(nullptr, NS_EINVAL, "event %d: term_value must be > 0", e);
-  return NS_OK;
+  return flow_check_config(c, e);
 }
 
 static int check_event(const ns_event& ev, int e) {
@@ -311,6 +311,14 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
     ns_free(h);
     return set_error(nullptr, NS_ECUDA, "event table upload: %s", cudaGetErrorString(e0));
   }
+  for (int e = 0; e < n_events; ++e) {
+    int r = flow_setup(h, e);
+    if (r) {
+      std::string msg = h->err;
+      ns_free(h);
+      return set_error(nullptr, r, "%s", msg.c_str());
+    }
+  }
   int r = nested_init(h);
   if (r) {
     std::string msg = h->err;
@@ -432,6 +440,9 @@ extern "C" int ns_walk_batch(ns_handle* h, int event, const double* live_u, int 
   T.event = event;
   T.spec = E.cfg.spec_depth > 0 ? E.cfg.spec_depth : default_spec(h->precision);
   cudaError_t e;
+  if ((e = cudaMemsetAsync(h->d_status + 1, 0, sizeof(int32_t), s)) != cudaSuccess) return cuda_fail(h, e, "status reset");
+  int fr = flow_attach(h, event, T, n, n_steps, &h->scratch_flow, s);
+  if (fr) return fr;
   // block -> (event, walker) maps, one task slot of the handle
   int r = ensure_scratch(h, h->scratch_map, sizeof(int32_t) * 2 * (size_t)n + sizeof(WalkTask));
   if (r) return r;
@@ -488,12 +499,16 @@ extern "C" void ns_free(ns_handle* h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   nested_free(h);
-  for (auto& E : h->events) free_event(E);
+  for (auto& E : h->events) {
+    free_event(E);
+    flow_free(E);
+  }
   cudaFree(h->d_events);
   cudaFree(h->d_status);
   cudaFree(h->scratch_in.ptr);
   cudaFree(h->scratch_out.ptr);
   cudaFree(h->scratch_map.ptr);
+  cudaFree(h->scratch_flow.ptr);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }

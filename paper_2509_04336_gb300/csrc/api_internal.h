@@ -2,10 +2,12 @@
 #pragma once
 
 #include <cstdint>
+#include <cstdio>
 #include <string>
 #include <vector>
 
 #include "../../include/gwns.h"
+#include "flow_internal.h"
 #include "gwns_internal.h"
 
 namespace gwns {
@@ -56,6 +58,7 @@ struct EventHost {
   double* d_gw64 = nullptr;
   float* d_gw32 = nullptr;
   NsState ns;            // host mirror of the device pointers and static fields
+  FlowHost flow;         // flow proposal (enabled for NS_PROPOSAL_DE_FLOW)
 };
 
 }  // namespace gwns
@@ -69,7 +72,7 @@ struct ns_handle {
   std::vector<gwns::EventHost> events;
   gwns::EventDev* d_events = nullptr;
   int32_t* d_status = nullptr;
-  gwns::Scratch scratch_in, scratch_out, scratch_map;
+  gwns::Scratch scratch_in, scratch_out, scratch_map, scratch_flow;
   // nested sampling
   gwns::NsState* d_ns = nullptr;
   gwns::WalkTask* d_tasks = nullptr;
@@ -80,6 +83,7 @@ struct ns_handle {
   std::vector<cudaEvent_t> walk_events;  // [2 * batches in the graph]: start, end of each walk
   double walk_ms = 0.0;
   int64_t kernel_launches = 0;
+  int64_t launches_per_batch[9] = {};   // kernels in each cached graph, per batch count
   // speculation-depth autotuner (all events in automatic mode)
   bool tune = false;
   int tune_next = 3;                 // iteration at which the next tuning pass starts
@@ -96,3 +100,13 @@ int ensure_scratch(ns_handle* h, gwns::Scratch& s, size_t bytes);
 int nested_init(ns_handle* h);
 int default_spec(int precision);
 void nested_free(ns_handle* h);
+// flow proposal (flow_api.cu)
+int flow_check_config(const ns_config& c, int e);
+int flow_setup(ns_handle* h, int e);
+void flow_free(gwns::EventHost& E);
+void flow_task_fields(const gwns::EventHost& E, gwns::WalkTask& T);
+int flow_enqueue_train(ns_handle* h, int e, cudaStream_t s, int64_t* launches);
+int flow_enqueue_table(ns_handle* h, int e, cudaStream_t s, int64_t* launches);
+int flow_attach(ns_handle* h, int event, gwns::WalkTask& T, int n, int n_steps, gwns::Scratch* table, cudaStream_t s);
+bool flow_state_write(ns_handle* h, int e, FILE* f);
+bool flow_state_read(ns_handle* h, int e, FILE* f);

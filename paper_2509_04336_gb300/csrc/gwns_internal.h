@@ -34,6 +34,15 @@ struct WalkTask {
   int32_t done;
   int32_t event;           // index into the event table
   int32_t spec;            // proposals evaluated per round (1 .. kSpecMax)
+  // flow steps (null flow: DE only).  Step t of walker w is a flow step when Philox word
+  // (t, walker_offset + w, iteration, 6)[0] gives U < p_flow; its proposal and log q are
+  // entry (w, t) of the proposal table [n][f_stride].
+  const struct FlowDev* flow;
+  const double* fu;        // [n][f_stride][D]
+  const double* flq;       // [n][f_stride]
+  double p_flow;
+  int32_t f_stride;
+  int32_t pad_;
 };
 
 constexpr int kSpecMax = 32;   // speculation depth limit (one warp of proposals)

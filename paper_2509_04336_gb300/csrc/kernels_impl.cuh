@@ -11,6 +11,7 @@
 
 #include <cstdio>
 
+#include "flow.cuh"
 #include "gwns_internal.h"
 
 namespace gwns {
@@ -325,6 +326,11 @@ __global__ void __launch_bounds__(256) waveform_kernel(const EventDev* __restric
 // The chain, the accepted and likelihood-call counts and every ln L are those of the walk
 // that takes one step at a time.  The setup warp rotates over the CTAs of an SM (an arrival
 // counter), so their FP64 work lands on different sub-partitions.
+// Flow steps (task.flow set): a step whose Philox tag-6 draw falls below p_flow proposes the
+// precomputed flow sample of the proposal table instead of a DE move, and passes the screen
+// iff ln U < ln q(u) - ln q(u') (an independence Metropolis-Hastings test taken before the
+// likelihood); ln q of the current point is carried along and re-evaluated on CUDA cores
+// after an accepted DE move.
 template <int PREC, int NDET, int WF>
 __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __restrict__ evs, WalkTask* tasks,
                                                          const int32_t* __restrict__ blk_task,
@@ -341,7 +347,11 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
   __shared__ double red[kWarps][kMaxVals];
   __shared__ double vals[kMaxVals];
   __shared__ int wcount[kWarps];
-  __shared__ int s_next, s_setup_warp, s_nin, s_end;
+  __shared__ int s_next, s_setup_warp, s_nin, s_end, s_needq;
+  __shared__ int s_isflow[kSpecMax];
+  __shared__ float s_lqf[kSpecMax];
+  __shared__ float s_logq;
+  __shared__ FlowScratch fscr;
   const WalkTask& T = tasks[blk_task[blockIdx.x]];
   const int j = blk_local[blockIdx.x];
   const EventDev& ev = evs[T.event];
@@ -371,13 +381,29 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
   const float de_scale32 = (float)de_scale;
   __syncthreads();
   const int sw = s_setup_warp;
+  const bool use_flow = T.flow != nullptr && T.p_flow > 0.0;
+  const double p_flow = T.p_flow;
+  if (use_flow) {
+    const float lq = flow_logq_cta(*T.flow, u, fscr);
+    if (threadIdx.x == 0) s_logq = lq;
+    __syncthreads();
+  }
   int t = 0;
   while (t < n_steps) {
     const int W = min(window, n_steps - t);
     // 1a. every thread screens one candidate step in FP32
     int maybe = 0;
     const int step = t + (int)threadIdx.x;
-    if ((int)threadIdx.x < W) {
+    bool fl = false;
+    if (use_flow && (int)threadIdx.x < W) {
+      Philox4 C = philox4x64((uint64_t)step, wid, it, 6ull, T.key0, T.key1);
+      if (rand_open_unit(C.v[0]) < p_flow) {
+        fl = true;
+        const float lqf = (float)T.flq[(size_t)j * T.f_stride + step];
+        maybe = logf((float)rand_open_unit(C.v[1])) < s_logq - lqf;
+      }
+    }
+    if ((int)threadIdx.x < W && !fl) {
       Philox4 A = philox4x64((uint64_t)step, wid, it, 0ull, T.key0, T.key1);
       uint64_t a = rand_index(A.v[0], n_s);
       uint64_t b = rand_index(A.v[1], n_s - 1);
@@ -435,10 +461,23 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
     // 1b. the setup warp redoes the maybe-in-bounds steps exactly (FP64, as the walk is
     //     defined) and compacts the in-bounds ones into at most m slots
     if (warp == sw) {
-      int in = 0;
+      int in = 0, isf = 0;
+      float lqf = 0.0f;
       double pr[kMaxDim];
       const int st = lane < nmaybe ? mstep[lane] : 0;
-      if (lane < nmaybe) {
+      if (use_flow && lane < nmaybe) {
+        Philox4 C = philox4x64((uint64_t)st, wid, it, 6ull, T.key0, T.key1);
+        if (rand_open_unit(C.v[0]) < p_flow) {
+          isf = 1;
+          lqf = (float)T.flq[(size_t)j * T.f_stride + st];
+          in = logf((float)rand_open_unit(C.v[1])) < s_logq - lqf;
+          const double* fu = T.fu + ((size_t)j * T.f_stride + st) * D;
+#pragma unroll
+          for (int d = 0; d < kMaxDim; ++d)
+            if (d < D) pr[d] = fu[d];
+        }
+      }
+      if (lane < nmaybe && !isf) {
         Philox4 A = philox4x64((uint64_t)st, wid, it, 0ull, T.key0, T.key1);
         uint64_t a = rand_index(A.v[0], n_s);
         uint64_t b = rand_index(A.v[1], n_s - 1);
@@ -474,6 +513,8 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
         for (int d = 0; d < kMaxDim; ++d)
           if (d < D) prop[slot][d] = pr[d];
         cstep[slot] = st;
+        s_isflow[slot] = isf;
+        s_lqf[slot] = lqf;
       }
       const int nin_w = min(__popc(im), m);
       // steps covered by this round: up to the m-th in-bounds proposal, else up to the last
@@ -526,6 +567,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
     // 3. the steps in order
     if (threadIdx.x == 0) {
       int nxt = s_end + 1;
+      s_needq = 0;
       for (int i = 0; i < nin; ++i) {
         ++n_like;
         n_bins += P[i].k_end;
@@ -534,6 +576,10 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
           lnl = lnl_p[i];
           ++n_acc;
           nxt = cstep[i] + 1;
+          if (use_flow) {
+            if (s_isflow[i]) s_logq = s_lqf[i];
+            else s_needq = 1;
+          }
           break;
         }
       }
@@ -542,6 +588,11 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
     }
     __syncthreads();
     t = s_next;
+    if (use_flow && s_needq && t < n_steps) {
+      const float lq = flow_logq_cta(*T.flow, u, fscr);
+      if (threadIdx.x == 0) s_logq = lq;
+      __syncthreads();
+    }
   }
   if (threadIdx.x < D) T.u_out[(size_t)j * D + threadIdx.x] = u[threadIdx.x];
   if (threadIdx.x == 0) {

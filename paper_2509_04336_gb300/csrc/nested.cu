@@ -399,11 +399,17 @@ int ensure_dead_capacity(ns_handle* h, int batches) {
   return NS_OK;
 }
 
-int enqueue_batch(ns_handle* h, int b) {
+int enqueue_batch(ns_handle* h, int b, int64_t* launches) {
   const int ne = (int)h->events.size();
+  int r;
+  for (int ev = 0; ev < ne; ++ev)
+    if ((r = flow_enqueue_train(h, ev, h->stream, launches))) return r;
   select_kernel<<<ne, kSelThreads, 0, h->stream>>>(h->d_ns, h->d_tasks);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "select launch");
+  for (int ev = 0; ev < ne; ++ev)
+    if ((r = flow_enqueue_table(h, ev, h->stream, launches))) return r;
+  *launches += 3;
   // inside stream capture a plain event record is only a dependency marker; the external
   // flag makes it an event-record node that timestamps every replay
   if ((e = cudaEventRecordWithFlags(h->walk_events[2 * b], h->stream, cudaEventRecordExternal)) != cudaSuccess)
@@ -429,10 +435,12 @@ int build_graph(ns_handle* h, int batches) {
   }
   e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+  int64_t launches = 0;
   for (int b = 0; b < batches; ++b) {
-    int r = enqueue_batch(h, b);
+    int r = enqueue_batch(h, b, &launches);
     if (r) { cudaStreamEndCapture(h->stream, &g); return r; }
   }
+  h->launches_per_batch[batches] = launches;
   e = cudaStreamEndCapture(h->stream, &g);
   if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
   e = cudaGraphInstantiate(&h->graph_exec[batches], g, 0);
@@ -502,6 +510,7 @@ int nested_init(ns_handle* h) {
     T.lnl_star = -INFINITY; T.iteration = 0; T.walker_offset = 0;
     T.key0 = S.key0; T.key1 = S.key1; T.n_s = S.n_live - S.k; T.n = S.k; T.n_steps = S.n_steps;
     T.done = 0; T.event = e;
+    flow_task_fields(E, T);
     total_walkers += S.k;
   }
   if ((r = alloc(h, (void**)&h->d_ns, sizeof(NsState) * ne, "states")) ||
@@ -637,7 +646,7 @@ extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
       if (e != cudaSuccess) return cuda_fail(h, e, "walk timing");
       h->walk_ms += ms;
     }
-    h->kernel_launches += 3 * (int64_t)b;
+    h->kernel_launches += h->launches_per_batch[b];
     if (trial) {
       int64_t like1 = 0;
       for (auto& S : h->host_ns) like1 += S.n_like;
@@ -753,7 +762,7 @@ extern "C" int ns_posterior(ns_handle* h, int event, double* theta_out, double* 
 
 // ---------------------------------------------------------------- checkpoint / resume
 namespace {
-const char kMagic[8] = {'G', 'W', 'N', 'S', 'S', 'T', '0', '1'};
+const char kMagic[8] = {'G', 'W', 'N', 'S', 'S', 'T', '0', '2'};
 
 bool wr(FILE* f, const void* p, size_t n) { return fwrite(p, 1, n, f) == n; }
 bool rd(FILE* f, void* p, size_t n) { return fread(p, 1, n, f) == n; }
@@ -788,6 +797,7 @@ extern "C" int ns_state_save(ns_handle* h, const char* path) {
     ok = ok && dev_write(f, S.live_u, (size_t)S.n_live * S.D) && dev_write(f, S.live_lnl, (size_t)S.n_live);
     ok = ok && dev_write(f, S.dead_u, (size_t)S.n_dead * S.D) && dev_write(f, S.dead_lnl, (size_t)S.n_dead);
     ok = ok && dev_write(f, S.dead_logw, (size_t)S.n_dead) && dev_write(f, S.dead_nlive, (size_t)S.n_dead);
+    ok = ok && flow_state_write(h, e, f);
   }
   ok = (fclose(f) == 0) && ok;
   return ok ? NS_OK : set_error(h, NS_EIO, "writing %s failed", path);
@@ -813,6 +823,7 @@ extern "C" int ns_state_load(ns_handle* h, const char* path) {
     ok = ok && dev_read(f, E.ns.live_u, (size_t)S.n_live * S.D) && dev_read(f, E.ns.live_lnl, (size_t)S.n_live);
     ok = ok && dev_read(f, E.ns.dead_u, (size_t)S.n_dead * S.D) && dev_read(f, E.ns.dead_lnl, (size_t)S.n_dead);
     ok = ok && dev_read(f, E.ns.dead_logw, (size_t)S.n_dead) && dev_read(f, E.ns.dead_nlive, (size_t)S.n_dead);
+    ok = ok && flow_state_read(h, e, f);
   }
   fclose(f);
   if (!ok) return set_error(h, NS_EIO, "reading %s failed or it does not match this handle", path);

@@ -106,6 +106,9 @@ extern "C" int ns_walk_batch_noalloc(ns_handle* h, int event, const double* live
   T.event = event;
   T.spec = E.cfg.spec_depth > 0 ? E.cfg.spec_depth : default_spec(h->precision);
   cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+  // flow steps draw on the handle's own proposal table, allocated at ns_init
+  r = flow_attach(h, event, T, n, n_steps, nullptr, s);
+  if (r) return r;
   fill_walk_scratch<<<(n + 255) / 256, 256, 0, s>>>(scratch, T, n);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "scratch fill launch");
   WalkTask* d_task = (WalkTask*)scratch;

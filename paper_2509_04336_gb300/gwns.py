@@ -24,6 +24,7 @@ NS_OK, NS_EINVAL, NS_ECUDA, NS_ENOMEM, NS_ENONFINITE, NS_ETIMEOUT, NS_ESTATE, NS
 NS_WMAXMCMC = 1
 NS_PTR_HOST, NS_PTR_DEVICE = 0, 1
 NS_PREC_FP64, NS_PREC_MIXED, NS_PREC_MIXED_FF = 0, 1, 2
+NS_PROPOSAL_DE, NS_PROPOSAL_DE_FLOW = 0, 1
 STATUS_NAMES = {0: "NS_OK", -1: "NS_EINVAL", -2: "NS_ECUDA", -3: "NS_ENOMEM", -4: "NS_ENONFINITE",
                 -5: "NS_ETIMEOUT", -6: "NS_ESTATE", -7: "NS_EIO", 1: "NS_WMAXMCMC"}
 
@@ -38,7 +39,9 @@ class ns_config(C.Structure):
                 ("naccept", C.c_int32), ("maxmcmc", C.c_int32), ("delay", C.c_double),
                 ("use_ratio", C.c_int32), ("term_kind", C.c_int32), ("term_value", C.c_double),
                 ("precision", C.c_int32), ("waveform", C.c_int32), ("max_iter", C.c_int32),
-                ("n_steps0", C.c_int32), ("seed", C.c_uint64), ("spec_depth", C.c_int32), ("reserved", C.c_int32)]
+                ("n_steps0", C.c_int32), ("seed", C.c_uint64), ("spec_depth", C.c_int32), ("proposal", C.c_int32),
+                ("p_flow", C.c_double), ("flow_layers", C.c_int32), ("flow_every", C.c_int32),
+                ("flow_epochs", C.c_int32), ("reserved", C.c_int32), ("flow_lr", C.c_double)]
 
 
 class ns_detector(C.Structure):
@@ -63,7 +66,9 @@ class ns_progress(C.Structure):
 
 
 EXPORTS = ("ns_init", "ns_waveform", "ns_likelihood_batch", "ns_walk_batch", "ns_step", "ns_evidence",
-           "ns_posterior", "ns_state_save", "ns_state_load", "ns_walk_batch_noalloc", "ns_free", "ns_last_error")
+           "ns_posterior", "ns_state_save", "ns_state_load", "ns_walk_batch_noalloc", "ns_flow_num_params",
+           "ns_flow_set", "ns_flow_get", "ns_flow_logq", "ns_flow_sample", "ns_flow_grad", "ns_flow_train",
+           "ns_free", "ns_last_error")
 
 _lib = None
 
@@ -88,6 +93,13 @@ def load(path: str = LIB_PATH):
     lib.ns_state_save.argtypes = [P, C.c_char_p]
     lib.ns_state_load.argtypes = [P, C.c_char_p]
     lib.ns_walk_batch_noalloc.argtypes = [P, I, P, I, P, P, D, I, I, C.c_int64, C.c_int64, P, P, P, P, V]
+    lib.ns_flow_num_params.argtypes = [P, I, C.POINTER(C.c_int32)]
+    lib.ns_flow_set.argtypes = [P, I, P, P, P]
+    lib.ns_flow_get.argtypes = [P, I, P, P, P]
+    lib.ns_flow_logq.argtypes = [P, I, P, I, P, I, V]
+    lib.ns_flow_sample.argtypes = [P, I, C.c_int64, C.c_int64, I, I, P, P, I, V]
+    lib.ns_flow_grad.argtypes = [P, I, P, I, P, C.POINTER(C.c_double)]
+    lib.ns_flow_train.argtypes = [P, I, P, I, I, P]
     lib.ns_free.argtypes = [P]
     lib.ns_free.restype = None
     lib.ns_last_error.argtypes = [P]
@@ -135,7 +147,9 @@ def _same_kind(*arrays):
 
 # ---------------------------------------------------------------- marshalling helpers
 def make_config(w: synth.Workload, priors=None, *, precision=None, max_iter=0, n_steps0=0, delay=-1.0,
-                seed=None, spec_depth=0) -> ns_config:
+                seed=None, spec_depth=0, p_flow=None, flow_layers=0, flow_every=0, flow_epochs=0,
+                flow_lr=0.0) -> ns_config:
+    """ns_config of a workload; p_flow (not None) selects NS_PROPOSAL_DE_FLOW."""
     c = ns_config()
     pri = w.priors if priors is None else priors
     for i, p in enumerate(pri):
@@ -149,6 +163,10 @@ def make_config(w: synth.Workload, priors=None, *, precision=None, max_iter=0, n
     c.max_iter, c.n_steps0 = max_iter, n_steps0
     c.seed = w.seed if seed is None else seed
     c.spec_depth = spec_depth
+    if p_flow is not None:
+        c.proposal = NS_PROPOSAL_DE_FLOW
+        c.p_flow = p_flow
+        c.flow_layers, c.flow_every, c.flow_epochs, c.flow_lr = flow_layers, flow_every, flow_epochs, flow_lr
     return c
 
 
@@ -255,6 +273,57 @@ def ns_state_save(h, path: str):
 
 def ns_state_load(h, path: str):
     return _check(_lib.ns_state_load(h, path.encode()), h)
+
+
+def ns_flow_num_params(h, event: int = 0) -> int:
+    n = C.c_int32()
+    _check(_lib.ns_flow_num_params(h, event, C.byref(n)), h)
+    return n.value
+
+
+def ns_flow_set(h, event: int, params, mu, sigma):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    s = np.ascontiguousarray(sigma, dtype=np.float64)
+    return _check(_lib.ns_flow_set(h, event, p.ctypes.data, m.ctypes.data, s.ctypes.data), h)
+
+
+def ns_flow_get(h, event: int, n_dim: int):
+    """(params float32 [n_params], mu [D], sigma [D])."""
+    p = np.zeros(ns_flow_num_params(h, event), dtype=np.float32)
+    m = np.zeros(n_dim)
+    s = np.zeros(n_dim)
+    _check(_lib.ns_flow_get(h, event, p.ctypes.data, m.ctypes.data, s.ctypes.data), h)
+    return p, m, s
+
+
+def ns_flow_logq(h, event: int, u, logq):
+    (pu, kind, st), (pl, _, _) = _same_kind(u, logq)
+    return _check(_lib.ns_flow_logq(h, event, pu, u.shape[0], pl, kind, st), h)
+
+
+def ns_flow_sample(h, event: int, iteration: int, walker_offset: int, u_out, logq_out):
+    """u_out [n][n_steps][D], logq_out [n][n_steps]."""
+    (pu, kind, st), (pl, _, _) = _same_kind(u_out, logq_out)
+    return _check(_lib.ns_flow_sample(h, event, iteration, walker_offset, u_out.shape[0], u_out.shape[1], pu, pl,
+                                      kind, st), h)
+
+
+def ns_flow_grad(h, event: int, u):
+    """(mean -ln q, gradient float32 [n_params]) of host points u [n][D]."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    g = np.zeros(ns_flow_num_params(h, event), dtype=np.float32)
+    loss = C.c_double()
+    _check(_lib.ns_flow_grad(h, event, u.ctypes.data, u.shape[0], g.ctypes.data, C.byref(loss)), h)
+    return loss.value, g
+
+
+def ns_flow_train(h, event: int, u, epochs: int):
+    """Losses before each of the epochs Adam steps on host points u [n][D]."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    losses = np.zeros(max(epochs, 1))
+    _check(_lib.ns_flow_train(h, event, u.ctypes.data, u.shape[0], epochs, losses.ctypes.data), h)
+    return losses[:epochs]
 
 
 def ns_free(h):

@@ -81,6 +81,11 @@ def _event_and_config():
     (lambda c, e: setattr(e, "df", -1.0), gwns.NS_EINVAL),
     (lambda c, e: e.det[0].psd.__setitem__(3, -1.0), gwns.NS_ENONFINITE),
     (lambda c, e: e.det[1].d_re.__setitem__(0, float("nan")), gwns.NS_ENONFINITE),
+    (lambda c, e: setattr(c, "proposal", 5), gwns.NS_EINVAL),
+    (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_DE_FLOW), setattr(c, "p_flow", 1.5)), gwns.NS_EINVAL),
+    (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_DE_FLOW), setattr(c, "flow_layers", 17)), gwns.NS_EINVAL),
+    (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_DE_FLOW), setattr(c, "flow_lr", -1.0)), gwns.NS_EINVAL),
+    (lambda c, e: setattr(c, "reserved", 1), gwns.NS_EINVAL),
 ])
 def test_init_rejects_bad_input_without_device_work(lib, mutate, code):
     w, ev = _event_and_config()
@@ -97,4 +102,7 @@ def test_init_rejects_bad_input_without_device_work(lib, mutate, code):
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.ns_likelihood_batch(None, 0, None, 0, None, 0, None) == gwns.NS_EINVAL
     assert lib.ns_step(None, 1, None) == gwns.NS_EINVAL
+    n = C.c_int32()
+    assert lib.ns_flow_num_params(None, 0, C.byref(n)) == gwns.NS_EINVAL
+    assert lib.ns_flow_logq(None, 0, None, 0, None, 0, None) == gwns.NS_EINVAL
     lib.ns_free(None)

@@ -164,8 +164,13 @@ def test_adam_first_step_is_signed_learning_rate():
     g = np.array([3.0, -2.0, 1e-3, -1e-5, 0.0])
     p = a.step(np.zeros(5), g)
     np.testing.assert_allclose(p, -0.01 * g / (np.abs(g) + F.ADAM_EPS), rtol=1e-12, atol=0)
-    assert np.all(a.step(p, np.array([np.nan, 0, 0, 0, 0])) == p)   # non-finite: skipped
-    assert a.t == 1
+    m0 = a.m.copy()
+    p2 = a.step(p, np.array([np.nan, 0, 0, 0, 0]))   # a non-finite component is skipped
+    assert p2[0] == p[0] and a.m[0] == m0[0] and a.t == 2
+    # the others take an ordinary second step: m = 0.9 m1, v = 0.999 v1
+    mh = 0.9 * m0[1:] / (1 - 0.9 ** 2)
+    vh = 0.999 * (0.001 * g[1:] ** 2) / (1 - 0.999 ** 2)
+    np.testing.assert_allclose(p2[1:], p[1:] - 0.01 * mh / (np.sqrt(vh) + F.ADAM_EPS), rtol=1e-12, atol=1e-15)
 
 
 def test_initial_flow_is_standardised_identity():
