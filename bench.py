@@ -52,7 +52,8 @@ NCU_WALK_TRAFFIC_BYTES = {"bbh11_3det_4s_taylorf2": 337664 + 16384, "bbh11_3det_
 
 
 def rank_info():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+    from paper_2509_04336_gb300 import shard
+    return shard.rank_info()
 
 
 # ---------------------------------------------------------------- event synthesis
@@ -94,11 +95,12 @@ def library_event(w: synth.Workload, seed_offset: int, device: int):
 
 def build_events(name: str, rank: int, device: int):
     """Workloads and library-made events of a named bench workload."""
+    from paper_2509_04336_gb300 import shard
     if name == "batched64":
-        ws = synth.batched_workloads(64, seed=100 + 1000 * rank)
+        ws = shard.rank_population(64, rank)
         out = [library_event(w, 0, device) for w in ws]
         return [w for w, _ in out], [e for _, e in out]
-    w, ev = library_event(synth.workload(name), rank, device)
+    w, ev = library_event(synth.workload(name), shard.single_event_seed_offset(rank), device)
     return [w], [ev]
 
 
@@ -109,6 +111,10 @@ WORKLOAD_DESCRIPTIONS = {
                              "11 params, n_live 2000, num_delete 1000, naccept 60, SNR 30, seeded noise",
     "batched64": "batched64: 64 events in one handle, IMRPhenomD form, 3 detectors, 4/8/16 s "
                  "(4017/16,225/32,449 bins), Mc U[10,60], SNR U[12,40], n_live U{500..2000}, num_delete n_live/2",
+    "bbh11_3det_8s_phenomd_flow": "bbh11_3det_8s_phenomd_flow: 3 detectors, 16,225 bins (8 s, 20-2048 Hz), "
+                                  "IMRPhenomD form, 11 params, n_live 4000, num_delete 2000, naccept 60, SNR 30, "
+                                  "seeded noise; DE + flow proposals (8 coupling layers, hidden 128, bf16 tensor "
+                                  "cores), flow retrained on the survivors every batch (50 Adam steps, lr 3e-3)",
 }
 
 
@@ -252,8 +258,14 @@ def run_ours(args):
     ne = len(evs)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def configs(precision):
-        return [gwns.make_config(wi, synth.priors_with_injection(wi, ei), precision=precision) for wi, ei in zip(ws, evs)]
+    flow_run = args.workload.endswith("_flow")
+
+    def configs(precision, p_flow=None):
+        if flow_run and p_flow is None:
+            p_flow = args.p_flow
+        kw = {} if p_flow is None else {"p_flow": p_flow, "flow_layers": 8}
+        return [gwns.make_config(wi, synth.priors_with_injection(wi, ei), precision=precision, **kw)
+                for wi, ei in zip(ws, evs)]
 
     def total(progress):
         keys = ("n_like", "n_bins", "n_spec")
@@ -261,8 +273,9 @@ def run_ours(args):
         out.update({k: progress[0][k] for k in ("walk_ms", "kernel_launches", "spec_depth", "n_steps", "mean_accept")})
         return out
 
-    def timed_steps(precision, steps, warmup, sample_clocks=False):
-        h = gwns.ns_init(configs(precision), evs, local)
+    def timed_steps(precision, steps, warmup, sample_clocks=False, p_flow=None):
+        h = gwns.ns_init(configs(precision, p_flow), evs, local)
+        accepted = 0.0
         try:
             for _ in range(warmup):
                 gwns.ns_step(h, 1, ne)
@@ -284,6 +297,7 @@ def run_ours(args):
                 e1.record()
                 torch.cuda.synchronize()
                 ms += e0.elapsed_time(e1)
+                accepted += sum(pi["mean_accept"] * wi.num_delete for pi, wi in zip(p, ws))
             if clocks:
                 clocks.__exit__()
             torch.cuda.synchronize()
@@ -294,23 +308,38 @@ def run_ours(args):
                    "bins": p1["n_bins"] - p0[0]["n_bins"], "walk_ms": p1["walk_ms"] - p0[0]["walk_ms"],
                    "spec": p1["n_spec"] - p0[0]["n_spec"],
                    "launches": p1["kernel_launches"] - p0[0]["kernel_launches"], "progress": p1,
-                   "clocks": clocks.summary() if clocks else None}
+                   "accepted": accepted, "clocks": clocks.summary() if clocks else None}
             return res
         finally:
             gwns.ns_free(h)
 
     mixed = timed_steps(synth.PREC_MIXED_FF, args.steps, args.warmup, sample_clocks=True)
-    mixed64 = timed_steps(synth.PREC_MIXED, args.steps, args.warmup)
-    plain = timed_steps(synth.PREC_FP64, args.steps, args.warmup)
+    sweep = None
+    if flow_run:
+        # the plain FP64 walk at 4000 live points takes seconds a batch: the flow line compares
+        # proposals instead, every arm in the float-float mode
+        sweep = {}
+        for pf in (0.0, 0.5, 0.9):
+            r = mixed if pf == args.p_flow else timed_steps(synth.PREC_MIXED_FF, args.steps, args.warmup, p_flow=pf)
+            sweep[str(pf)] = {"lnl_evals_per_s": r["evals"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / args.steps,
+                              "accepted_steps_per_s": r["accepted"] / (r["ms"] * 1e-3),
+                              "accepted_per_lnl_call": r["accepted"] / max(r["evals"], 1),
+                              "walk_ms_per_step": r["walk_ms"] / args.steps}
+        mixed64 = plain = None
+    else:
+        mixed64 = timed_steps(synth.PREC_MIXED, args.steps, args.warmup)
+        plain = timed_steps(synth.PREC_FP64, args.steps, args.warmup)
 
     t_max = reduce(mixed["ms"], dist.ReduceOp.MAX if dist else None)
     evals = reduce(float(mixed["evals"]), dist.ReduceOp.SUM if dist else None)
     value = evals / (t_max * 1e-3)
-    t_plain = reduce(plain["ms"], dist.ReduceOp.MAX if dist else None)
-    evals_plain = reduce(float(plain["evals"]), dist.ReduceOp.SUM if dist else None)
-    value_plain = evals_plain / (t_plain * 1e-3)
-    t_m64 = reduce(mixed64["ms"], dist.ReduceOp.MAX if dist else None)
-    value_m64 = reduce(float(mixed64["evals"]), dist.ReduceOp.SUM if dist else None) / (t_m64 * 1e-3)
+    value_plain = value_m64 = t_plain = t_m64 = None
+    if plain is not None:
+        t_plain = reduce(plain["ms"], dist.ReduceOp.MAX if dist else None)
+        evals_plain = reduce(float(plain["evals"]), dist.ReduceOp.SUM if dist else None)
+        value_plain = evals_plain / (t_plain * 1e-3)
+        t_m64 = reduce(mixed64["ms"], dist.ReduceOp.MAX if dist else None)
+        value_m64 = reduce(float(mixed64["evals"]), dist.ReduceOp.SUM if dist else None) / (t_m64 * 1e-3)
 
     # end to end through the public API with host buffers: init (host data upload and the
     # initial live points), K batches, evidence read back
@@ -360,9 +389,13 @@ def run_ours(args):
                    "precision": "mixed: FP32 sums, float-float phase, FP64 per-walker constants and lnL assembly",
                    "step": "one sampler batch (select, walk, insert)",
                    "l2": "flushed (256 MB write) between timed steps", "events_per_rank": ne},
-        "plain_fp64": {"value": value_plain, "unit": UNIT, "ms_per_step": t_plain / args.steps},
-        "mixed_fp64_phase": {"value": value_m64, "unit": UNIT, "ms_per_step": t_m64 / args.steps},
-        "mixed_over_plain": value / value_plain,
+        "plain_fp64": None if plain is None else {"value": value_plain, "unit": UNIT,
+                                                  "ms_per_step": t_plain / args.steps},
+        "mixed_fp64_phase": None if plain is None else {"value": value_m64, "unit": UNIT,
+                                                        "ms_per_step": t_m64 / args.steps},
+        "mixed_over_plain": None if plain is None else value / value_plain,
+        "p_flow": args.p_flow if flow_run else None,
+        "p_flow_sweep": sweep,
         "speculative_evals_per_eval": mixed["spec"] / max(mixed["evals"], 1),
         "spec_depth": mixed["progress"]["spec_depth"],
         "mean_walk_steps": mixed["progress"]["n_steps"], "mean_accept": mixed["progress"]["mean_accept"],
@@ -396,7 +429,9 @@ def run_profile_case(args):
     gwns.load()
     torch.cuda.set_device(0)
     ws, evs = build_events(args.workload, 0, 0)
-    cfgs = [gwns.make_config(w, synth.priors_with_injection(w, e), precision=args.precision) for w, e in zip(ws, evs)]
+    kw = {"p_flow": args.p_flow, "flow_layers": 8} if args.workload.endswith("_flow") else {}
+    cfgs = [gwns.make_config(w, synth.priors_with_injection(w, e), precision=args.precision, **kw)
+            for w, e in zip(ws, evs)]
     h = gwns.ns_init(cfgs, evs)
     try:
         for _ in range(args.profile_batches):
@@ -417,6 +452,7 @@ def main():
     ap.add_argument("--profile-batches", type=int, default=0,
                     help="run this many batches of the workload without timing (a small case for ncu)")
     ap.add_argument("--precision", type=int, default=synth.PREC_MIXED_FF)
+    ap.add_argument("--p-flow", type=float, default=0.5, help="flow-step probability of the *_flow workloads")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCRIPTIONS),
                     help="bench workload (the default is the headline line)")
     args = ap.parse_args()

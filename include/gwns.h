@@ -119,9 +119,9 @@ typedef struct ns_config {
     double p_flow;        /* DE_FLOW: probability that a walk step is a flow step, [0, 1] */
     int32_t flow_layers;  /* DE_FLOW: affine coupling layers, 1..16 (0: 8)            */
     int32_t flow_every;   /* DE_FLOW: retrain the flow every this many batches (0: 1)  */
-    int32_t flow_epochs;  /* DE_FLOW: full-batch Adam steps per retraining (0: 20)     */
+    int32_t flow_epochs;  /* DE_FLOW: full-batch Adam steps per retraining (0: 50)     */
     int32_t reserved;     /* must be 0                                              */
-    double flow_lr;       /* DE_FLOW: Adam learning rate (0: 1e-3)                  */
+    double flow_lr;       /* DE_FLOW: Adam learning rate (0: 3e-3)                  */
 } ns_config;
 
 /* One detector's data.  Pointers are HOST arrays of n_bins doubles, copied by ns_init. */
@@ -254,9 +254,10 @@ int ns_state_load(ns_handle* h, const char* path);
  *   ln U < ln q(u) - ln q(u') (word 1) and ln L(u') > ln L* -- a Metropolis-Hastings step
  *   that keeps the prior restricted to L > L* invariant.  The q test comes first, so a
  *   rejected flow step costs no likelihood call.
- *   Training: maximum likelihood on the n_live current points at the start of every
- *   flow_every-th batch (mu, sigma re-estimated; flow_epochs full-batch Adam steps,
- *   beta (0.9, 0.999), eps 1e-8; weights and Adam state carry over).
+ *   Training: maximum likelihood on the n_live - k survivors (samples of the prior above
+ *   the new L*) of every flow_every-th batch, after the deletion: mu, sigma re-estimated,
+ *   flow_epochs full-batch Adam steps (beta (0.9, 0.999), eps 1e-8); weights and Adam state
+ *   carry over from batch to batch.
  * Parameters are a flat FP32 vector, per layer W1 [128][D], b1 [128], W2 [128][128],
  * b2 [128], W3 [2D][128] (rows: s_0..s_{D-1}, t_0..t_{D-1}), b3 [2D]; ns_flow_num_params
  * gives its length.  Every call below returns NS_ESTATE for an event without a flow.

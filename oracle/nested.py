@@ -17,11 +17,12 @@ One batch (iteration `it`) of the sampler:
      not printed -- parity unpinned);
   5. stop when ln(Z + L_max X) - ln Z < dlogZ (Sec. 4.1.1), or, for the fractional rule,
      when the live evidence L_mean X is below the given fraction of Z (Sec. 4.2).
-With a flow (p_flow > 0; survey rows a11/a12, motivated in Sec. 6): the flow starts from
-oracle.flow.init_flow and, at the start of every batch it % flow_every == 0, before the
-deletion, is re-standardised and trained for flow_epochs full-batch Adam steps on the n_live
-current points (warm start: weights and Adam state persist); the walk then mixes flow
-steps with probability p_flow (oracle.walk).
+With a flow (p_flow > 0; the paper only motivates flows, Sec. 6): the flow starts from
+oracle.flow.init_flow and, in every batch it % flow_every == 0, after the deletion, is
+re-standardised and trained for flow_epochs full-batch Adam steps on the n_live - k
+survivors, which sample the prior above the new L* that the walks target (warm start:
+weights and Adam state persist); the walk then mixes flow steps with probability p_flow
+(oracle.walk).
 The final live points each receive weight L_i X / n.  The logZ error is the standard
 deviation over replays that draw every shrinkage factor t ~ Beta(n_j, 1).
 Initial live points: u[i, d] from Philox block (i, d // 4, 0, 3), word d % 4.
@@ -110,7 +111,7 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
                periodic, key, term_kind: int = TERM_DLOGZ, term_value: float = 0.1,
                delay: float | None = None, max_iter: int = 100000, n_replay: int = 200,
                initial_u=None, n_steps0: int | None = None, replay_seed: int = 12345,
-               p_flow: float = 0.0, flow_every: int = 1, flow_epochs: int = 20, flow_lr: float = 1e-3,
+               p_flow: float = 0.0, flow_every: int = 1, flow_epochs: int = 50, flow_lr: float = 3e-3,
                flow_hidden: int = 128, flow_layers: int = 8, flow_bf16: bool = False) -> NestedResult:
     k = num_delete
     if delay is None:
@@ -129,8 +130,6 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
         adam = flowmod.Adam(flow.flat().size, flow_lr)
     it = 0
     while it < max_iter:
-        if flow is not None and it % flow_every == 0:
-            flowmod.train(flow, u, flow_epochs, adam, flow_bf16)
         order = np.lexsort((np.arange(n_live), lnl))
         dead, surv = order[:k], order[k:]
         lnl_star = lnl[dead[-1]]
@@ -144,6 +143,8 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
             dead_lnl.append(lnl[idx])
             dead_logw.append(log_w)
             dead_nlive.append(nj)
+        if flow is not None and it % flow_every == 0:
+            flowmod.train(flow, u[surv], flow_epochs, adam, flow_bf16)
         starts = surv[start_indices(k, it, n_live - k, key)]
         new_u, new_lnl, n_acc, n_call, _ = acceptance_walk(
             loglike, u[starts], lnl[starts], lnl_star, u[surv], n_steps, periodic, key, it,

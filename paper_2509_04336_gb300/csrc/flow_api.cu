@@ -1,11 +1,11 @@
 // flow_api.cu -- the flow proposal's buffers, its place in a sampler batch, and the ns_flow_*
 // entry points of the C ABI.
 //
-// In a batch of an event configured with NS_PROPOSAL_DE_FLOW the graph runs, before the
+// In a batch of an event configured with NS_PROPOSAL_DE_FLOW the graph runs, after the
 // deletion, a flag kernel (retrain when iteration % flow_every == 0), the standardisation and
-// flow_epochs pairs of (gradient, Adam) launches on the n_live current points -- each
-// returns at once when the flag is clear -- and, after the deletion, the proposal table of
-// the batch's walks (one inverse-flow sample and its ln q for every (walker, step)).
+// flow_epochs pairs of (gradient, Adam) launches on the n_live - k survivors -- each returns
+// at once when the flag is clear -- and then the proposal table of the batch's walks (one
+// inverse-flow sample and its ln q for every (walker, step)).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -96,8 +96,8 @@ int flow_setup(ns_handle* h, int e) {
   Fh.enabled = 1;
   Fh.n_layers = c.flow_layers > 0 ? c.flow_layers : 8;
   Fh.every = c.flow_every > 0 ? c.flow_every : 1;
-  Fh.epochs = c.flow_epochs > 0 ? c.flow_epochs : 20;
-  Fh.lr = c.flow_lr > 0.0 ? c.flow_lr : 1e-3;
+  Fh.epochs = c.flow_epochs > 0 ? c.flow_epochs : 50;
+  Fh.lr = c.flow_lr > 0.0 ? c.flow_lr : 3e-3;
   Fh.p_flow = c.p_flow;
   Fh.n_params = Fh.n_layers * flow_layer_params(E.n_dim);
   Fh.tiles_cap = kTilesCap;
@@ -155,15 +155,16 @@ int flow_enqueue_train(ns_handle* h, int e, cudaStream_t s, int64_t* launches) {
   FlowHost& Fh = E.flow;
   if (!Fh.enabled) return NS_OK;
   const NsState& S = E.ns;
+  const int n_surv = S.n_live - S.k;   // the survivors sample the prior above the new L*
   flow_train_flag_kernel<<<1, 32, 0, s>>>(h->d_ns + e, Fh.every, Fh.d_train);
   cudaError_t err = cudaGetLastError();
-  if (!err) err = launch_flow_standardise(Fh.d_flow, S.live_u, S.n_live, Fh.d_train, s);
+  if (!err) err = launch_flow_standardise(Fh.d_flow, S.surv_u, n_surv, Fh.d_train, s);
   *launches += 2;
   for (int ep = 0; ep < Fh.epochs && !err; ++ep) {
-    err = launch_flow_grad(Fh.d_flow, S.live_u, S.n_live, Fh.d_train, 1, Fh.d_partial, Fh.d_loss_part, Fh.d_zsave,
+    err = launch_flow_grad(Fh.d_flow, S.surv_u, n_surv, Fh.d_train, 1, Fh.d_partial, Fh.d_loss_part, Fh.d_zsave,
                            h->d_status + 1, s);
     if (!err)
-      err = launch_flow_adam(Fh.d_flow, Fh.d_img, Fh.d_bias, Fh.d_master, Fh.d_m, Fh.d_v, Fh.d_partial, S.n_live,
+      err = launch_flow_adam(Fh.d_flow, Fh.d_img, Fh.d_bias, Fh.d_master, Fh.d_m, Fh.d_v, Fh.d_partial, n_surv,
                              Fh.d_train, nullptr, Fh.n_params, s);
     *launches += 2;
   }

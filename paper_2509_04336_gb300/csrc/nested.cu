@@ -402,13 +402,12 @@ int ensure_dead_capacity(ns_handle* h, int batches) {
 int enqueue_batch(ns_handle* h, int b, int64_t* launches) {
   const int ne = (int)h->events.size();
   int r;
-  for (int ev = 0; ev < ne; ++ev)
-    if ((r = flow_enqueue_train(h, ev, h->stream, launches))) return r;
   select_kernel<<<ne, kSelThreads, 0, h->stream>>>(h->d_ns, h->d_tasks);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "select launch");
   for (int ev = 0; ev < ne; ++ev)
-    if ((r = flow_enqueue_table(h, ev, h->stream, launches))) return r;
+    if ((r = flow_enqueue_train(h, ev, h->stream, launches)) || (r = flow_enqueue_table(h, ev, h->stream, launches)))
+      return r;
   *launches += 3;
   // inside stream capture a plain event record is only a dependency marker; the external
   // flag makes it an event-record node that timestamps every replay

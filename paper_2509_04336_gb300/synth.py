@@ -198,6 +198,7 @@ def workload(name: str) -> Workload:
                                injection at SNR 39.6, 11 parameters, 1000 live points.
     bbh11_3det_8s_phenomd      3 detectors, 20-2048 Hz at 0.125 Hz (16,225 bins), Table 4
                                injection at SNR 30, IMRPhenomD-form waveform, 2000 live points.
+    bbh11_3det_8s_phenomd_flow the same with 4000 live points (k = 2000), for flow proposals.
     """
     if name == "four_param_2det_taylorf2":
         inj = np.array([28.0, 0.8, 0.3, -0.2, 1000.0, 0.40, 2.66, 1.30, 0.0, 1.38, -1.21])
@@ -218,6 +219,9 @@ def workload(name: str) -> Workload:
         return Workload(name, ("H", "L", "V"), 20.0, 2048.0, 8.0, PHENOMD_FORM, TABLE4_INJECTION.copy(),
                         30.0, True, pri, n_live=2000, num_delete=1000, naccept=60, maxmcmc=5000,
                         term_kind=TERM_DLOGZ, term_value=0.1, seed=2, precision=PREC_MIXED)
+    if name == "bbh11_3det_8s_phenomd_flow":
+        # the 8 s workload with 4000 live points, for the flow-proposal runs
+        return replace(workload("bbh11_3det_8s_phenomd"), name=name, n_live=4000, num_delete=2000)
     raise KeyError(name)
 
 
@@ -290,7 +294,7 @@ def batched_workloads(n_events: int = 64, seed: int = 100, waveform: int = PHENO
     three quarters of the events are stratified over the three durations so that each
     appears at least n_events/4 times (20-1024 Hz at 4 s, 20-2048 Hz at 8 and 16 s: 4017,
     16,225 and 32,449 bins); n_live ~ U{500, 600, ..., 2000}, num_delete = n_live / 2;
-    priors Mc +- 25 % around the injection, q [0.25, 1], spins [-0.8, 0.8]; noise seed 100 + e.
+    priors Mc +- 25 % around the injection, q [0.25, 1], spins [-0.8, 0.8]; noise seed `seed` + e.
     """
     rng = np.random.Generator(np.random.Philox(key=np.array([seed, 4444], dtype=np.uint64)))
     out = []
@@ -313,6 +317,6 @@ def batched_workloads(n_events: int = 64, seed: int = 100, waveform: int = PHENO
         pri = _standard_priors((0.75 * mc, 1.25 * mc), (0.25, 1.0), (-0.8, 0.8))
         w = Workload(f"batched_{e}", ("H", "L", "V"), 20.0, f_max, duration, waveform, inj, snr, True, pri,
                      n_live=n_live, num_delete=n_live // 2, naccept=60, maxmcmc=5000,
-                     term_kind=TERM_DLOGZ, term_value=0.1, seed=100 + e, precision=precision)
+                     term_kind=TERM_DLOGZ, term_value=0.1, seed=seed + e, precision=precision)
         out.append(w)
     return out
