@@ -64,6 +64,9 @@ __device__ __forceinline__ bool flow_cond(int l, int d) { return ((d + l) & 1) =
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+// tanh of the flow's activations (one definition for every kernel that evaluates the flow).
+__device__ __forceinline__ float flow_tanh(float x) { return tanhf(x); }
+
 // z0 and -log(u (1 - u)) of one coordinate (FP32 logarithms; 1 - u formed in FP64).
 __device__ __forceinline__ void flow_pre_map(const FlowDev& F, int d, double u, float& z0, float& jac) {
   const float lu = logf((float)u), l1u = logf((float)(1.0 - u));
@@ -115,7 +118,7 @@ static __device__ __noinline__ float flow_logq_cta(const FlowDev& F, const doubl
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc = fmaf(w[i], S.a[8 * c + i], acc);
       }
-      S.h1[tid] = bf16_round(tanhf(acc));
+      S.h1[tid] = bf16_round(flow_tanh(acc));
     }
     __syncthreads();
     {  // hidden layer 2: unit tid
@@ -126,7 +129,7 @@ static __device__ __noinline__ float flow_logq_cta(const FlowDev& F, const doubl
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc = fmaf(w[i], S.h1[8 * c + i], acc);
       }
-      S.h2[tid] = bf16_round(tanhf(acc));
+      S.h2[tid] = bf16_round(flow_tanh(acc));
     }
     __syncthreads();
     {  // outputs: output tid / 4, quarter tid % 4 of its 128 inputs
@@ -144,7 +147,7 @@ static __device__ __noinline__ float flow_logq_cta(const FlowDev& F, const doubl
     }
     __syncthreads();
     if (tid < D && !flow_cond(l, tid)) {
-      const float s = kFlowS * tanhf(S.o[tid] / kFlowS);
+      const float s = kFlowS * flow_tanh(S.o[tid] / kFlowS);
       S.z[tid] = S.z[tid] * expf(s) + S.o[16 + tid];
       sdet += s;
     }

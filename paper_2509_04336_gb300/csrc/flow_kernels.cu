@@ -31,13 +31,14 @@ namespace {
 
 constexpr int kFT = 128;
 
-// apply kernel shared memory (bytes)
-constexpr uint32_t kApWF0 = 0, kApWF1 = 45056, kApXA = 90112, kApHA = 94208, kApBar = 126976;
+// apply kernel shared memory (bytes): two weight buffers, two bias buffers, a, h
+constexpr uint32_t kBiasBytes = kBiasLayer * 4;   // 1152
+constexpr uint32_t kApWF0 = 0, kApWF1 = 45056, kApB0 = 90112, kApB1 = 91264, kApXA = 92416, kApHA = 96512;
+constexpr uint32_t kApBar = 129280;
 constexpr uint32_t kApBytes = kApBar + 64;
 // gradient kernel shared memory (bytes)
-constexpr uint32_t kGrXA = 0, kGrXAT = 4096, kGrHA = 8192, kGrHAT = 40960, kGrHB = 73728, kGrHBT = 106496;
-constexpr uint32_t kGrG3 = 139264, kGrG3T = 147456, kGrWF = 155648, kGrW1T = 200704, kGrW3T = 204800;
-constexpr uint32_t kGrCS = 212992, kGrBar = 215040;
+constexpr uint32_t kGrXA = 0, kGrHA = 4096, kGrHB = 36864, kGrG3 = 69632, kGrWF = 77824, kGrW1T = 122880;
+constexpr uint32_t kGrW3T = 126976, kGrCS = 135168, kGrBias = 137216, kGrBar = 138368;
 constexpr uint32_t kGrBytes = kGrBar + 64;
 static_assert(kGrBytes <= 232448, "gradient kernel shared memory");
 
@@ -64,10 +65,6 @@ __device__ __forceinline__ void st_row16(unsigned char* img, int r, int c0, cons
 __device__ __forceinline__ void ld_row16(const unsigned char* img, int r, int c0, float* v) {
   bf16x8(*reinterpret_cast<const uint4*>(img + tc::image_offset(128, r, c0)), v);
   bf16x8(*reinterpret_cast<const uint4*>(img + tc::image_offset(128, r, c0 + 8)), v + 8);
-}
-// element (r, c) of a row image written transposed: entry (c, r) of an R-row image
-__device__ __forceinline__ void st_t(unsigned char* img, int R, int c, int r, float v) {
-  *reinterpret_cast<__nv_bfloat16*>(img + tc::image_offset(R, c, r)) = __float2bfloat16_rn(v);
 }
 
 // Sum over the warp's 32 lanes of column `lane` of the lanes' 32-column vectors v (the
@@ -108,6 +105,16 @@ struct Tc {
     for (int k = 0; k < ksteps; ++k)
       tc::mma_bf16(tmem + dcol, tc::sdesc(a0 + 2u * k * albo, albo, 128), tc::sdesc(b0 + 2u * k * blbo, blbo, 128),
                    id, k > 0 ? 1u : 0u);
+  }
+  // D (+)= A^T B over K = 16 ksteps of the tile's points: A and B are 128-row images read
+  // MN-major (their columns are D's rows and columns).
+  __device__ void gemm_mn(uint32_t dcol, const unsigned char* A, const unsigned char* B, int N, int ksteps) const {
+    const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
+    const uint32_t lbo = 128, sbo = tc::image_lbo(128);
+    const uint32_t id = tc::idesc_bf16_mn(128, N, true, true);
+    for (int k = 0; k < ksteps; ++k)
+      tc::mma_bf16(tmem + dcol, tc::sdesc(a0 + 256u * k, lbo, sbo), tc::sdesc(b0 + 256u * k, lbo, sbo), id,
+                   k > 0 ? 1u : 0u);
   }
   __device__ void commit() {
     tc::mma_commit(mbar);
@@ -180,6 +187,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_apply_kernel(ApplyArgs A) {
   unsigned char* WF[2] = {sm + kApWF0, sm + kApWF1};
   unsigned char* XA = sm + kApXA;
   unsigned char* HA = sm + kApHA;
+  float* BS[2] = {reinterpret_cast<float*>(sm + kApB0), reinterpret_cast<float*>(sm + kApB1)};
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kApBar);   // [0], [1] weights, [2] MMA
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kApBar + 32);
   int* abort = reinterpret_cast<int*>(sm + kApBar + 36);
@@ -250,7 +258,9 @@ __global__ void __launch_bounds__(kFT, 1) flow_apply_kernel(ApplyArgs A) {
     for (int li = 0; li < L && ok; ++li, ++s) {
       const int l = layer_of(s);
       const int b = s & 1;
-      const float* bias = F.bias + (size_t)l * kBiasLayer;
+      // this step's biases (the buffer of step s - 1 is still being read until the barrier)
+      float* bias = BS[b];
+      for (int i = tid; i < kBiasLayer; i += kFT) bias[i] = __ldg(F.bias + (size_t)l * kBiasLayer + i);
       if (tid == 0 && s + 1 < total) issue(s + 1);
       {
         float a[kFlowP];
@@ -279,7 +289,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_apply_kernel(ApplyArgs A) {
         float v[16];
         T.ld16(c0, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = tanhf(v[i] + __ldg(bias + kBiasB1 + c0 + i));
+        for (int i = 0; i < 16; ++i) v[i] = flow_tanh(v[i] + bias[kBiasB1 + c0 + i]);
         st_row16(HA, tid, c0, v);
       }
       Tc::publish();
@@ -295,7 +305,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_apply_kernel(ApplyArgs A) {
         float v[16];
         T.ld16(c0, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = tanhf(v[i] + __ldg(bias + kBiasB2 + c0 + i));
+        for (int i = 0; i < 16; ++i) v[i] = flow_tanh(v[i] + bias[kBiasB2 + c0 + i]);
         st_row16(HA, tid, c0, v);
       }
       Tc::publish();
@@ -312,8 +322,8 @@ __global__ void __launch_bounds__(kFT, 1) flow_apply_kernel(ApplyArgs A) {
 #pragma unroll
         for (int d = 0; d < kFlowP; ++d)
           if (d < D && !flow_cond(l, d)) {
-            const float sc = kFlowS * tanhf((sr[d] + __ldg(bias + kBiasB3 + d)) / kFlowS);
-            const float sh = tt[d] + __ldg(bias + kBiasB3 + 16 + d);
+            const float sc = kFlowS * flow_tanh((sr[d] + bias[kBiasB3 + d]) / kFlowS);
+            const float sh = tt[d] + bias[kBiasB3 + 16 + d];
             z[d] = A.inverse ? (z[d] - sh) * expf(-sc) : z[d] * expf(sc) + sh;
             logdet += sc;
           }
@@ -379,10 +389,10 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
   const bool valid = row < G.n;
   if (G.bump_t && tile == 0 && tid == 0) F.adam_t += 1;
 
-  unsigned char *XA = sm + kGrXA, *XAT = sm + kGrXAT, *HA = sm + kGrHA, *HAT = sm + kGrHAT;
-  unsigned char *HB = sm + kGrHB, *HBT = sm + kGrHBT, *G3 = sm + kGrG3, *G3T = sm + kGrG3T;
+  unsigned char *XA = sm + kGrXA, *HA = sm + kGrHA, *HB = sm + kGrHB, *G3 = sm + kGrG3;
   unsigned char *WF = sm + kGrWF, *W1T = sm + kGrW1T, *W3T = sm + kGrW3T;
   float* CS = reinterpret_cast<float*>(sm + kGrCS);             // [4 warps][128]
+  float* bias = reinterpret_cast<float*>(sm + kGrBias);         // this layer's b1 | b2 | b3
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kGrBar);   // [0] weights, [1] W2T, [2] MMA
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kGrBar + 32);
   int* abort = reinterpret_cast<int*>(sm + kGrBar + 36);
@@ -414,6 +424,10 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
     if (tid < 32) out[tid] = CS[tid] + CS[128 + tid] + CS[256 + tid] + CS[384 + tid];
     __syncthreads();
   };
+  // this layer's biases into shared memory (the previous readers passed a barrier)
+  auto stage_bias = [&](int l) {
+    for (int i = tid; i < kBiasLayer; i += kFT) bias[i] = __ldg(F.bias + (size_t)l * kBiasLayer + i);
+  };
 
   // ---- forward pass: layer inputs saved, log q for the loss
   float z[kFlowP], jac = 0.0f, logdet = 0.0f;
@@ -430,7 +444,6 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       }
   }
   for (int l = 0; l < L && ok; ++l) {
-    const float* bias = F.bias + (size_t)l * kBiasLayer;
     float4* zsl = reinterpret_cast<float4*>(zs + ((size_t)l * kFT + tid) * kFlowP);
 #pragma unroll
     for (int q = 0; q < 4; ++q) zsl[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
@@ -439,6 +452,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       tc::bulk_g2s(WF, F.img + (size_t)l * kImgLayer, kImgFwd, &bars[0]);
       wpend = 1;
     }
+    stage_bias(l);
     {
       float a[kFlowP];
 #pragma unroll
@@ -465,7 +479,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       float v[16];
       T.ld16(c0, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = tanhf(v[i] + __ldg(bias + kBiasB1 + c0 + i));
+      for (int i = 0; i < 16; ++i) v[i] = flow_tanh(v[i] + bias[kBiasB1 + c0 + i]);
       st_row16(HA, tid, c0, v);
     }
     Tc::publish();
@@ -480,7 +494,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       float v[16];
       T.ld16(c0, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = tanhf(v[i] + __ldg(bias + kBiasB2 + c0 + i));
+      for (int i = 0; i < 16; ++i) v[i] = flow_tanh(v[i] + bias[kBiasB2 + c0 + i]);
       st_row16(HB, tid, c0, v);
     }
     Tc::publish();
@@ -497,13 +511,13 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
 #pragma unroll
       for (int d = 0; d < kFlowP; ++d)
         if (d < D && !flow_cond(l, d)) {
-          const float sc = kFlowS * tanhf((sr[d] + __ldg(bias + kBiasB3 + d)) / kFlowS);
-          z[d] = z[d] * expf(sc) + tt[d] + __ldg(bias + kBiasB3 + 16 + d);
+          const float sc = kFlowS * flow_tanh((sr[d] + bias[kBiasB3 + d]) / kFlowS);
+          z[d] = z[d] * expf(sc) + tt[d] + bias[kBiasB3 + 16 + d];
           logdet += sc;
         }
     }
     tc::fence_before_sync();
-    __syncthreads();   // WF is reloaded by the next layer
+    __syncthreads();   // WF and the biases are reloaded by the next layer
   }
   // loss part: sum over the tile's points of -log q
   float g[kFlowP];
@@ -526,7 +540,6 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
 
   // ---- backward pass
   for (int l = L - 1; l >= 0 && ok; --l) {
-    const float* bias = F.bias + (size_t)l * kBiasLayer;
     const unsigned char* img = F.img + (size_t)l * kImgLayer;
     float* pl = part + (size_t)l * LP;
     float zin[kFlowP];
@@ -545,13 +558,12 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       tc::bulk_g2s(W3T, img + kImgW3T, 8192, &bars[0]);
       wpend = 1;
     }
+    stage_bias(l);
     {
       float a[kFlowP];
 #pragma unroll
       for (int d = 0; d < kFlowP; ++d) a[d] = (d < D && flow_cond(l, d)) ? zin[d] : 0.0f;
       st_row16(XA, tid, 0, a);
-#pragma unroll
-      for (int d = 0; d < kFlowP; ++d) st_t(XAT, 16, d, tid, a[d]);
     }
     Tc::publish();
     if (tid == 0) {
@@ -568,16 +580,13 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
     __syncthreads();
     if (*abort) { ok = false; break; }
     if (!(ok = T.wait())) break;
-    // h1 -> HA, HAT
+    // h1 -> HA
 #pragma unroll 1
     for (int c0 = 0; c0 < kFlowH; c0 += 16) {
       float v[16];
       T.ld16(c0, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        v[i] = tanhf(v[i] + __ldg(bias + kBiasB1 + c0 + i));
-        st_t(HAT, 128, c0 + i, tid, v[i]);
-      }
+      for (int i = 0; i < 16; ++i) v[i] = flow_tanh(v[i] + bias[kBiasB1 + c0 + i]);
       st_row16(HA, tid, c0, v);
     }
     Tc::publish();
@@ -592,16 +601,13 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       tc::bulk_g2s(WF + kImgW2, img + kImgW2T, 32768, &bars[1]);
       w2pend = 1;
     }
-    // h2 -> HB, HBT
+    // h2 -> HB
 #pragma unroll 1
     for (int c0 = 0; c0 < kFlowH; c0 += 16) {
       float v[16];
       T.ld16(c0, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        v[i] = tanhf(v[i] + __ldg(bias + kBiasB2 + c0 + i));
-        st_t(HBT, 128, c0 + i, tid, v[i]);
-      }
+      for (int i = 0; i < 16; ++i) v[i] = flow_tanh(v[i] + bias[kBiasB2 + c0 + i]);
       st_row16(HB, tid, c0, v);
     }
     Tc::publish();
@@ -611,7 +617,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       T.commit();
     }
     if (!(ok = T.wait())) break;
-    // coupling backward: g_o = [d/ds_raw | d/dt] -> G3, G3T; db3; direct part of dz_in
+    // coupling backward: g_o = [d/ds_raw | d/dt] -> G3; db3; direct part of dz_in
     float gdir[kFlowP];
     {
       float sr[16], tt[16], go[32];
@@ -623,7 +629,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
         go[16 + d] = 0.0f;
         gdir[d] = g[d];
         if (d < D && !flow_cond(l, d)) {
-          const float th = tanhf((sr[d] + __ldg(bias + kBiasB3 + d)) / kFlowS);
+          const float th = flow_tanh((sr[d] + bias[kBiasB3 + d]) / kFlowS);
           const float e = expf(kFlowS * th);
           const float gs = valid ? (g[d] * zin[d] * e - 1.0f) : 0.0f;
           go[d] = gs * (1.0f - th * th);
@@ -633,8 +639,6 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       }
       st_row16(G3, tid, 0, go);
       st_row16(G3, tid, 16, go + 16);
-#pragma unroll
-      for (int o = 0; o < kFlowO; ++o) st_t(G3T, 32, o, tid, go[o]);
       float cs[32];
       colsum32(go, cs);   // go is consumed
       if (tid < kFlowO) {
@@ -646,8 +650,8 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
     Tc::publish();
     if (tid == 0) {
       tc::fence_after_sync();
-      T.gemm(0, G3, W3T, 128, 2);        // dh2 = g_o W3
-      T.gemm(128, HBT, G3T, 32, 8);      // dW3^T = h2^T g_o
+      T.gemm(0, G3, W3T, 128, 2);         // dh2 = g_o W3
+      T.gemm_mn(128, HB, G3, 32, 8);      // dW3^T = h2^T g_o
       T.commit();
     }
     if (!(ok = T.wait())) break;
@@ -665,7 +669,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
         }
       }
     }
-    // g_p2 = dh2 (1 - h2^2) -> G2 over HB, G2T over HBT; db2
+    // g_p2 = dh2 (1 - h2^2) -> G2 over HB; db2
 #pragma unroll 1
     for (int c0 = 0; c0 < kFlowH; c0 += 32) {
       float gp[32], h[16];
@@ -679,8 +683,6 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       for (int i = 0; i < 16; ++i) gp[16 + i] *= 1.0f - h[i] * h[i];
       st_row16(HB, tid, c0, gp);
       st_row16(HB, tid, c0 + 16, gp + 16);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) st_t(HBT, 128, c0 + i, tid, gp[i]);
       float cs[32];
       colsum32(gp, cs);
       if (tid < 32) pl[flow_off_b2(D) + c0 + tid] = cs[tid];
@@ -694,7 +696,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
         w2par ^= 1u;
         w2pend = 0;
         T.gemm(0, HB, WF + kImgW2, 128, 8);     // dh1 = g_p2 W2 (W2T image in the W2 slot)
-        T.gemm(128, HBT, HAT, 128, 8);          // dW2 = g_p2^T h1
+        T.gemm_mn(128, HB, HA, 128, 8);         // dW2 = g_p2^T h1
         T.commit();
       }
     }
@@ -712,7 +714,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
         for (int i = 0; i < 16; ++i) dst[i] = v[i];
       }
     }
-    // g_p1 = dh1 (1 - h1^2) -> G1 over HA, G1T over HAT; db1
+    // g_p1 = dh1 (1 - h1^2) -> G1 over HA; db1
 #pragma unroll 1
     for (int c0 = 0; c0 < kFlowH; c0 += 32) {
       float gp[32], h[16];
@@ -726,8 +728,6 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       for (int i = 0; i < 16; ++i) gp[16 + i] *= 1.0f - h[i] * h[i];
       st_row16(HA, tid, c0, gp);
       st_row16(HA, tid, c0 + 16, gp + 16);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) st_t(HAT, 128, c0 + i, tid, gp[i]);
       float cs[32];
       colsum32(gp, cs);
       if (tid < 32) pl[flow_off_b1(D) + c0 + tid] = cs[tid];
@@ -735,8 +735,8 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
     Tc::publish();
     if (tid == 0) {
       tc::fence_after_sync();
-      T.gemm(128, HA, W1T, 16, 8);     // g_a = g_p1 W1
-      T.gemm(192, HAT, XAT, 16, 8);    // dW1 = g_p1^T a
+      T.gemm(128, HA, W1T, 16, 8);       // g_a = g_p1 W1
+      T.gemm_mn(192, HA, XA, 16, 8);     // dW1 = g_p1^T a
       T.commit();
     }
     if (!(ok = T.wait())) break;
@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
       for (int d = 0; d < kFlowP; ++d) g[d] = gdir[d] + ((d < D && flow_cond(l, d)) ? v[d] : 0.0f);
     }
     tc::fence_before_sync();
-    __syncthreads();   // slots are reloaded by the next layer
+    __syncthreads();   // slots and biases are reloaded by the next layer
   }
   if (!ok && tid == 0) {
     if (wpend) tc::mbar_wait(&bars[0], wpar);

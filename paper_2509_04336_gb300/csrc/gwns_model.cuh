@@ -546,19 +546,35 @@ template <int NDET>
 __device__ __forceinline__ void bin_accumulate_ff(const EventDev& ev, const WalkerParams& p, int k,
                                                   AccF32& acc) {
   const float2* g = ev.basis_ff + (size_t)k * ev.n_basis;
-  float sh = p.ph0h, sl = p.ph0l;
+  // products C_j g_j as q_j + e_j (q_j = fl(Ch g.x); e_j its rounding error plus the Ch g.y and
+  // Cl g.x cross terms), then an error-free pairwise sum of the q_j (depth 3 instead of a chain
+  // of 8) whose errors join the low part
+  float q[kBasis];
+  float sl = p.ph0l;
 #pragma unroll
   for (int j = 0; j < kBasis; ++j) {
-    float2 gj = g[j];
-    float q = p.Ch[j] * gj.x;
-    float e = fmaf(p.Ch[j], gj.x, -q);
+    const float2 gj = g[j];
+    q[j] = p.Ch[j] * gj.x;
+    float e = fmaf(p.Ch[j], gj.x, -q[j]);
     e = fmaf(p.Ch[j], gj.y, e);
-    e = fmaf(p.Cl[j], gj.x, e);
-    float t = sh + q;
-    float bb = t - sh;
-    float err = (sh - (t - bb)) + (q - bb);
+    sl += fmaf(p.Cl[j], gj.x, e);
+  }
+#pragma unroll
+  for (int w = 1; w < kBasis; w <<= 1) {
+#pragma unroll
+    for (int j = 0; j + w < kBasis; j += 2 * w) {
+      const float t = q[j] + q[j + w];
+      const float bb = t - q[j];
+      sl += (q[j] - (t - bb)) + (q[j + w] - bb);
+      q[j] = t;
+    }
+  }
+  float sh;
+  {
+    const float t = p.ph0h + q[0];
+    const float bb = t - p.ph0h;
+    sl += (p.ph0h - (t - bb)) + (q[0] - bb);
     sh = t;
-    sl += err + e;
   }
   const float r0 = (sh - rintf(sh)) + sl;
   const float kf = (float)k;

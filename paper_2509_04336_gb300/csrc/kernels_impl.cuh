@@ -114,6 +114,65 @@ __device__ __forceinline__ void warp_reduce_f32(float* fv, float* fc) {
   }
 }
 
+// Compensated all-lane sums of NV values by recursive halving: at the exchange with offset
+// S each lane keeps half of the values it still carries (the upper half when bit S of its
+// lane is set) and adds its partner's copy of that half, so V = NV rounded up to a power of
+// two values need V - 1 pair exchanges before the last value is reduced over the remaining
+// lanes (instead of NV * 5).  Every addition is an error-free two-sum whose error joins the
+// compensation.  On return lane l holds the total (s, c) of value index
+// vbits(l) = bits 4, 3, ... of l read as the binary digits of the index (most significant
+// first), for log2 V digits.
+template <int V, int S>
+__device__ __forceinline__ void halve_step(float* s, float* c, int lane) {
+  const bool up = (lane & S) != 0;
+#pragma unroll
+  for (int i = 0; i < V / 2; ++i) {
+    const float ss = up ? s[i] : s[i + V / 2], sc = up ? c[i] : c[i + V / 2];
+    const float ks = up ? s[i + V / 2] : s[i], kc = up ? c[i + V / 2] : c[i];
+    const float os = __shfl_xor_sync(0xffffffffu, ss, S), oc = __shfl_xor_sync(0xffffffffu, sc, S);
+    float t, e;
+    two_sum(ks, os, t, e);
+    s[i] = t;
+    c[i] = kc + oc + e;
+  }
+}
+template <int S>
+__device__ __forceinline__ void fold_step(float& s, float& c) {
+  const float os = __shfl_xor_sync(0xffffffffu, s, S), oc = __shfl_xor_sync(0xffffffffu, c, S);
+  float t, e;
+  two_sum(s, os, t, e);
+  s = t;
+  c = c + oc + e;
+}
+template <int NV>
+struct Pow2Vals { static constexpr int value = NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : 16; };
+// (s, c) of the value this lane ends with; *index receives that value's index.
+template <int NV>
+__device__ __forceinline__ void warp_halving_sums(const float* fv, const float* fc, int lane, float& s_out,
+                                                  float& c_out, int& index) {
+  constexpr int V = Pow2Vals<NV>::value;
+  float s[V], c[V];
+#pragma unroll
+  for (int i = 0; i < V; ++i) { s[i] = i < NV ? fv[i] : 0.0f; c[i] = i < NV ? fc[i] : 0.0f; }
+  halve_step<V, 16>(s, c, lane);
+  if (V >= 4) halve_step<V / 2, 8>(s, c, lane);
+  if (V >= 8) halve_step<V / 4, 4>(s, c, lane);
+  if (V >= 16) halve_step<V / 8, 2>(s, c, lane);
+  float rs = s[0], rc = c[0];
+  if (V <= 8) fold_step<2>(rs, rc);
+  if (V <= 4) fold_step<4>(rs, rc);
+  if (V <= 2) fold_step<8>(rs, rc);
+  fold_step<1>(rs, rc);
+  int idx = 0;
+  idx = (idx << 1) | ((lane >> 4) & 1);
+  if (V >= 4) idx = (idx << 1) | ((lane >> 3) & 1);
+  if (V >= 8) idx = (idx << 1) | ((lane >> 2) & 1);
+  if (V >= 16) idx = (idx << 1) | ((lane >> 1) & 1);
+  s_out = rs;
+  c_out = rc;
+  index = idx;
+}
+
 // Sums of one walker over the whole CTA (stride kThreads), totals in `out` for thread 0.
 template <int PREC, int NDET, int WF>
 __device__ inline void cta_sums(const EventDev& ev, const WalkerParams& P, double (*red)[kMaxVals], double* out) {
@@ -542,9 +601,13 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
           warp_reduce_f64<NV>(dv);
           if (lane == 0) lnl_p[i] = lnl_from_vals<PREC, NDET, WF>(ev, P[i], dv);
         } else {
-          warp_reduce_f32<NV>(fv, fc);
-          if (lane == 0)
-            for (int q = 0; q < NV; ++q) { part_sums[i][2 * q] = fv[q]; part_sums[i][2 * q + 1] = fc[q]; }
+          float rs, rc;
+          int q;
+          warp_halving_sums<NV>(fv, fc, lane, rs, rc, q);
+          // the lanes that ended with distinct indices (the lowest lane of each group) store
+          constexpr int V = Pow2Vals<NV>::value;
+          constexpr int group = 32 / V;
+          if ((lane & (group - 1)) == 0 && q < NV) { part_sums[i][2 * q] = rs; part_sums[i][2 * q + 1] = rc; }
         }
       }
       if (PREC != 0) {

@@ -7,7 +7,12 @@
 // and cores adjacent along K R/8 * 128 bytes apart (the leading byte offset):
 //     byte(r, c) = ((c / 8) * (R / 8) + r / 8) * 128 + (r % 8) * 16 + (c % 8) * 2.
 // One tcgen05.mma of kind::f16 consumes K = 16 (two cores along K); the k-th K-slice of an
-// operand starts 2 k * LBO bytes further on.  The accumulator of an M = 128 MMA holds row i
+// operand starts 2 k * LBO bytes further on.
+// Read the other way round, the same bytes are an MN-major operand whose MN index is c and
+// whose K index is r: 8 MN-contiguous elements per 16-byte core row, 8 K rows 16 bytes apart,
+// cores adjacent along K 128 bytes apart (leading byte offset) and along MN R/8 * 128 bytes
+// apart (stride byte offset).  The weight gradients (K = the tile's points) use this, so the
+// activations are staged once, in row order.  The accumulator of an M = 128 MMA holds row i
 // in TMEM lane i, column j in column base + j (FP32).
 //
 // Every wait on an mbarrier is bounded: it gives up after kWaitLimit polls and reports the
@@ -29,6 +34,11 @@ __host__ __device__ constexpr uint32_t image_lbo(int R) { return (uint32_t)(R >>
 // Instruction descriptor of tcgen05.mma kind::f16: bf16 A and B (both K-major), FP32 D.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with A and/or B read MN-major (bits 15 and 16).
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N, bool a_mn, bool b_mn) {
+  return idesc_bf16(M, N) | (a_mn ? (1u << 15) : 0u) | (b_mn ? (1u << 16) : 0u);
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
