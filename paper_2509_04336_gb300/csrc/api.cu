@@ -203,8 +203,13 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
   D.df = in.df;
   D.gmst = in.gmst;
   D.dd_total = dd;
+  auto split = [](double x, float* f) { f[0] = (float)x; f[1] = (float)(x - (double)f[0]); };
+  split(in.f_min, D.fmin_f);
+  split(in.df, D.df_f);
+  split(in.gmst, D.gmst_f);
   for (int d = 0; d < nd; ++d)
     for (int i = 0; i < 3; ++i) {
+      split(in.det[d].vertex[i] / 299792458.0, D.vc_f[d][i]);
       D.vertex[d][i] = in.det[d].vertex[i];
       D.xarm[d][i] = in.det[d].x_arm[i];
       D.yarm[d][i] = in.det[d].y_arm[i];
@@ -234,7 +239,23 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
       q.A = std::sin(p.lo);
       q.B = std::sin(p.hi) - std::sin(p.lo);
     }
+    split(q.lo, q.lo_f);
+    split(q.w, q.w_f);
+    split(q.A, q.A_f);
+    split(q.B, q.B_f);
+    split(q.value, q.v_f);
+    split(q.cosv, q.cv_f);
+    split(q.sinv, q.sv_f);
+    q.einv_f = q.e != 0.0 ? (float)(1.0 / q.e) : 0.0f;
     if (p.kind != NS_PRIOR_FIXED) D.dim_param[nd_dim++] = i;
+  }
+  // the float-float setup transforms uniform priors, the power law of the distance, the sine
+  // prior of the inclination and the cosine prior of the declination
+  D.ff_setup = 1;
+  for (int i = 0; i < kParams; ++i) {
+    const int k = c.prior[i].kind;
+    if ((k == NS_PRIOR_POWERLAW && i != 4) || (k == NS_PRIOR_SINE && i != 5) || (k == NS_PRIOR_COSINE && i != 10))
+      D.ff_setup = 0;
   }
   D.n_dim = nd_dim;
   D.basis64 = E.d_basis64;

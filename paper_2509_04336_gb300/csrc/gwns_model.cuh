@@ -57,6 +57,9 @@ struct PriorDev {
   int kind;
   int periodic;
   double lo, hi, w, A, B, e, value, cosv, sinv;
+  // float-float copies (h, l) of lo, w, A, B, value, cos value, sin value
+  float lo_f[2], w_f[2], A_f[2], B_f[2], v_f[2], cv_f[2], sv_f[2];
+  float einv_f;   // 1 / (alpha + 1) of a power law
 };
 
 // Device copy of one event and its sampler configuration.
@@ -78,6 +81,10 @@ struct EventDev {
   const float* gw32;                   // [n_det][n_bins] FP32 copy scaled by 1/gw32_unscale (a power
                                        //   of two: the weights reach ~1e43, beyond FP32's range)
   double gw32_unscale;
+  // float-float copies of the geometry for the float-float proposal setup
+  int ff_setup;                        // 1 when every sampled prior has a float-float transform
+  float vc_f[kMaxDet][3][2];           // detector vertex / c [s]
+  float fmin_f[2], df_f[2], gmst_f[2];
 };
 
 // The IMRPhenomD-form part of the per-walker constants (in cycles).
@@ -611,3 +618,4 @@ __device__ inline double assemble_lnl(const EventDev& ev, const WalkerParams& p,
 }  // namespace gwns
 
 #include "gwns_phenomd.cuh"
+#include "ff_setup.cuh"

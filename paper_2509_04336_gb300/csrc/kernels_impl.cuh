@@ -227,6 +227,8 @@ __device__ inline void setup_from_unit(const EventDev& ev, const double* u, Walk
     double th[kParams], ci, sd, cd;
     unit_to_theta(ev, u, th, &ci, &sd, &cd);
     taylorf2_setup<WF>(ev, th, ci, sd, cd, P);
+  } else if (PREC == 2 && WF == 0 && ev.ff_setup) {
+    taylorf2_setup_ff(ev, u, P);
   } else {
     LeanTheta t;
     unit_to_lean(ev, u, t);
