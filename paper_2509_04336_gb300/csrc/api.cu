@@ -173,6 +173,10 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
   for (double v : gw64) gmax = std::fmax(gmax, v);
   const double gscale = gmax > 0.0 ? std::ldexp(1.0, -std::ilogb(gmax)) : 1.0;
   for (size_t i = 0; i < gw64.size(); ++i) gw32[i] = (float)(gw64[i] * gscale);
+  // FP32 copy of the template-power prefix sums scaled by 2^-140 (the float-float path pairs
+  // it with amplitude factors scaled by 2^70)
+  std::vector<float> pref32(pref.size());
+  for (size_t i = 0; i < pref.size(); ++i) pref32[i] = (float)std::ldexp(pref[i], -2 * kKpScaleExp);
   // device copies
   cudaError_t err;
   if ((err = cudaMalloc(&E.d_basis64, basis.size() * sizeof(double))) != cudaSuccess ||
@@ -181,7 +185,8 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
       (err = cudaMalloc(&E.d_z32, z32.size() * sizeof(float2))) != cudaSuccess ||
       (err = cudaMalloc(&E.d_hh_prefix, pref.size() * sizeof(double))) != cudaSuccess ||
       (err = cudaMalloc(&E.d_gw64, gw64.size() * sizeof(double))) != cudaSuccess ||
-      (err = cudaMalloc(&E.d_gw32, gw32.size() * sizeof(float))) != cudaSuccess)
+      (err = cudaMalloc(&E.d_gw32, gw32.size() * sizeof(float))) != cudaSuccess ||
+      (err = cudaMalloc(&E.d_hhp32, pref32.size() * sizeof(float))) != cudaSuccess)
     return set_error(nullptr, NS_ENOMEM, "event %d: device allocation failed: %s", e, cudaGetErrorString(err));
   if ((err = cudaMemcpy(E.d_basis64, basis.data(), basis.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMemcpy(E.d_basis_ff, basis_ff.data(), basis_ff.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -189,7 +194,8 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
       (err = cudaMemcpy(E.d_z32, z32.data(), z32.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMemcpy(E.d_hh_prefix, pref.data(), pref.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMemcpy(E.d_gw64, gw64.data(), gw64.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (err = cudaMemcpy(E.d_gw32, gw32.data(), gw32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      (err = cudaMemcpy(E.d_gw32, gw32.data(), gw32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(E.d_hhp32, pref32.data(), pref32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
     return set_error(nullptr, NS_ECUDA, "event %d: upload failed: %s", e, cudaGetErrorString(err));
 
   EventDev& D = E.dev;
@@ -263,6 +269,9 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
   D.z64 = E.d_z64;
   D.z32 = E.d_z32;
   D.hh_prefix = E.d_hh_prefix;
+  D.hhp32 = E.d_hhp32;
+  D.dd_f[0] = (float)dd;
+  D.dd_f[1] = (float)(dd - (double)D.dd_f[0]);
   D.gw64 = E.d_gw64;
   D.gw32 = E.d_gw32;
   D.gw32_unscale = 1.0 / gscale;
@@ -276,6 +285,8 @@ void free_event(EventHost& E) {
   cudaFree(E.d_z64);
   cudaFree(E.d_z32);
   cudaFree(E.d_hh_prefix);
+  cudaFree(E.d_hhp32);
+  E.d_hhp32 = nullptr;
   cudaFree(E.d_gw64);
   cudaFree(E.d_gw32);
   E.d_gw64 = nullptr;

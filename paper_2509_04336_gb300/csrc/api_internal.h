@@ -57,6 +57,7 @@ struct EventHost {
   double* d_hh_prefix = nullptr;
   double* d_gw64 = nullptr;
   float* d_gw32 = nullptr;
+  float* d_hhp32 = nullptr;
   NsState ns;            // host mirror of the device pointers and static fields
   FlowHost flow;         // flow proposal (enabled for NS_PROPOSAL_DE_FLOW)
 };

@@ -6,8 +6,9 @@
 // algorithms are the classical error-free transformations (Dekker 1971; Knuth's two-sum) and
 // their double-float compositions (as in Hida, Li & Bailey's QD library, reimplemented);
 // log and sin/cos use argument reduction and Taylor series written out from the mathematics.
-// Accuracy of each operation: a few units of 2^-44 relative (sums of values of one sign,
-// products, quotients, roots); log and sin/cos about 1e-13 absolute on the ranges used here.
+// Accuracy of each operation: a few units of 2^-44 relative (products, quotients, roots, sums
+// that do not cancel); log and sin/cos about 1e-13 absolute on the ranges used here -- far
+// below the 1e-6 cycle the phase needs.
 #pragma once
 
 #include <cstdint>
@@ -40,12 +41,11 @@ __device__ __forceinline__ ff two_prod_ff(float a, float b) {
   return ff{p, fmaf(a, b, -p)};
 }
 
+// The low parts are added without their own error term: relative error about 2^-44 times
+// (|a| + |b|) / |a + b|.  No sum in this library's uses cancels by more than a few digits.
 __device__ __forceinline__ ff ff_add(ff a, ff b) {
   ff s = two_sum_ff(a.h, b.h);
-  ff t = two_sum_ff(a.l, b.l);
-  s.l += t.h;
-  s = fast_two_sum_ff(s.h, s.l);
-  s.l += t.l;
+  s.l += a.l + b.l;
   return fast_two_sum_ff(s.h, s.l);
 }
 __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.h, -a.l}; }
@@ -82,23 +82,21 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {
   const float r = ((a.h - p.h) - p.l) + a.l;
   return fast_two_sum_ff(s, r / (2.0f * s));
 }
-// a^(-1/3), a > 0: FP32 seed, two Newton steps w <- w + w (1 - a w^3) / 3 with the residual
-// formed in float-float.
+// a^(-1/3), a > 0: FP32 seed (relative error ~1e-7), one Newton step w <- w + w (1 - a w^3)/3
+// with the residual formed in float-float (error ~1e-14 after it).
 __device__ __forceinline__ ff ff_rcbrt(ff a) {
   ff w = ff_make(rcbrtf(a.h));
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
+  {
     const ff t = ff_mul(a, ff_mul(ff_mul(w, w), w));
     const float r = (1.0f - t.h) - t.l;
     w = ff_add(w, ff_mul_f(w, r * (1.0f / 3.0f)));
   }
   return w;
 }
-// a^(-1/5), a > 0: z <- z + z (1 - a z^5) / 5.
+// a^(-1/5), a > 0: FP32 seed, one Newton step z <- z + z (1 - a z^5) / 5.
 __device__ __forceinline__ ff ff_rfifth(ff a) {
   ff z = ff_make(powf(a.h, -0.2f));
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
+  {
     const ff z2 = ff_mul(z, z);
     const ff t = ff_mul(a, ff_mul(ff_mul(z2, z2), z));
     const float r = (1.0f - t.h) - t.l;
@@ -108,8 +106,8 @@ __device__ __forceinline__ ff ff_rfifth(ff a) {
 }
 
 // ln a, a > 0: a = m 2^e with m in [1/sqrt 2, sqrt 2), ln a = e ln 2 + 2 atanh(y),
-// y = (m - 1) / (m + 1), |y| <= 0.1716, atanh(y) = y (1 + y^2/3 + y^4/5 + ... + y^20/21)
-// (truncation below 1e-17).
+// y = (m - 1) / (m + 1), |y| <= 0.1716, atanh(y) = y (1 + y^2/3 + y^4/5 + ... + y^16/17)
+// (truncation below 2e-15).
 __device__ __forceinline__ ff ff_log(ff a) {
   int e;
   float m = frexpf(a.h, &e);
@@ -117,9 +115,7 @@ __device__ __forceinline__ ff ff_log(ff a) {
   const ff x = ff_ldexp(a, -e);
   const ff y = ff_div(ff_add_f(x, -1.0f), ff_add_f(x, 1.0f));
   const ff y2 = ff_mul(y, y);
-  ff s = GWNS_FF(1.0 / 21.0);
-  s = ff_add(ff_mul(s, y2), GWNS_FF(1.0 / 19.0));
-  s = ff_add(ff_mul(s, y2), GWNS_FF(1.0 / 17.0));
+  ff s = GWNS_FF(1.0 / 17.0);
   s = ff_add(ff_mul(s, y2), GWNS_FF(1.0 / 15.0));
   s = ff_add(ff_mul(s, y2), GWNS_FF(1.0 / 13.0));
   s = ff_add(ff_mul(s, y2), GWNS_FF(1.0 / 11.0));
@@ -132,8 +128,29 @@ __device__ __forceinline__ ff ff_log(ff a) {
   return ff_add(ff_mul_f(GWNS_FF(0.6931471805599453), (float)e), at2);
 }
 
+// ln(U0 U1 U2 U3) for the open-unit uniforms U_i = ((x_i >> 12) + 1/2) / 2^52 of four Philox
+// words: each U_i as a float pair (the 53-bit numerator split exactly into 24 + 29 bits, the
+// low part rounded to 24), mantissas multiplied in [2^-4, 1) and the binary exponents summed,
+// so nothing underflows; one float-float logarithm.
+__device__ __forceinline__ ff ff_log_uniform_product(const uint64_t* x) {
+  ff prod = ff_make(1.0f);
+  int esum = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint64_t m2 = ((x[i] >> 12) << 1) | 1ull;        // 2 (x >> 12) + 1 < 2^53
+    const uint64_t hi = m2 & ~((1ull << 29) - 1ull);        // top 24 bits: exact in a float
+    ff u = fast_two_sum_ff((float)hi, (float)(m2 - hi));
+    int e;
+    frexpf(u.h, &e);
+    u = ff_ldexp(u, -e);                                    // u in [0.5, 1)
+    esum += e - 53;                                         // U_i = u 2^(e - 53)
+    prod = ff_mul(prod, u);
+  }
+  return ff_add(ff_log(prod), ff_mul_f(GWNS_FF(0.6931471805599453), (float)esum));
+}
+
 // sin and cos of a, |a| < 2^20: a = k pi/2 + r with |r| <= pi/4 (pi/2 as float + float pair),
-// Taylor series in r^2 to r^17 / r^16 (truncation below 1e-16), then the quadrant.
+// Taylor series in r^2 to r^15 / r^14 (truncation below 3e-14), then the quadrant.
 __device__ __forceinline__ void ff_sincos(ff a, ff& s_out, ff& c_out) {
   const float k = rintf(a.h * 0.63661977f);
   // pi/2 = P1 + P23: P1 = float(pi/2), P23 the remainder as a float pair
@@ -142,9 +159,8 @@ __device__ __forceinline__ void ff_sincos(ff a, ff& s_out, ff& c_out) {
   ff r = ff_sub(a, two_prod_ff(k, P1));             // k P1 exactly, as a pair
   r = ff_sub(r, ff_mul_f(P23, k));
   const ff r2 = ff_mul(r, r);
-  // sin r = r (1 - r^2/3! + r^4/5! - ... + r^16/17!)
-  ff ps = GWNS_FF(1.0 / 355687428096000.0);          // 1/17!
-  ps = ff_add(ff_mul(ps, r2), GWNS_FF(-1.0 / 1307674368000.0));
+  // sin r = r (1 - r^2/3! + r^4/5! - ... - r^14/15!)
+  ff ps = GWNS_FF(-1.0 / 1307674368000.0);           // -1/15!
   ps = ff_add(ff_mul(ps, r2), GWNS_FF(1.0 / 6227020800.0));
   ps = ff_add(ff_mul(ps, r2), GWNS_FF(-1.0 / 39916800.0));
   ps = ff_add(ff_mul(ps, r2), GWNS_FF(1.0 / 362880.0));
@@ -153,9 +169,8 @@ __device__ __forceinline__ void ff_sincos(ff a, ff& s_out, ff& c_out) {
   ps = ff_add(ff_mul(ps, r2), GWNS_FF(-1.0 / 6.0));
   ps = ff_add_f(ff_mul(ps, r2), 1.0f);
   const ff sr = ff_mul(r, ps);
-  // cos r = 1 - r^2/2! + r^4/4! - ... + r^16/16!
-  ff pc = GWNS_FF(1.0 / 20922789888000.0);           // 1/16!
-  pc = ff_add(ff_mul(pc, r2), GWNS_FF(-1.0 / 87178291200.0));
+  // cos r = 1 - r^2/2! + r^4/4! - ... - r^14/14!
+  ff pc = GWNS_FF(-1.0 / 87178291200.0);             // -1/14!
   pc = ff_add(ff_mul(pc, r2), GWNS_FF(1.0 / 479001600.0));
   pc = ff_add(ff_mul(pc, r2), GWNS_FF(-1.0 / 3628800.0));
   pc = ff_add(ff_mul(pc, r2), GWNS_FF(1.0 / 40320.0));

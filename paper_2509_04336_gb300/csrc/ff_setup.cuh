@@ -4,10 +4,10 @@
 // It computes what taylorf2_setup_lean followed by make_ff computes -- prior transform, masses,
 // the 3.5PN phase coefficients regrouped on the frequency basis, the phase constant, the
 // arrival delays and the split time shifts, the antenna patterns and the template power -- but
-// keeps FP64 only for the few operations whose inputs are FP64 (splitting the unit-cube
-// coordinates, the template-power product with the FP64 prefix sums).  With about 48
-// significant bits every coefficient is accurate far below what the phase needs (~1e-6 cycle),
-// and the FP64 pipe, shared by all the walkers of an SM, is left to the lnL assembly.
+// keeps FP64 only for splitting the unit-cube coordinates (FP64 inputs) into float pairs.  With about 48
+// significant bits every coefficient is accurate far below what the phase needs (~1e-6 cycle).
+// The amplitude factors K P_det are FP32, scaled by 2^70, and <h|h> comes from an FP32 copy of
+// the template-power prefix sums scaled by 2^-140; lnl_ff assembles ln L in float-float.
 #pragma once
 
 #include "ff.cuh"
@@ -153,9 +153,10 @@ __device__ inline void taylorf2_setup_ff(const EventDev& ev, const double* u, Wa
   const float X0 = spf * csf - ssf * cpf * ctf, X1 = -(cpf * csf + ssf * spf * ctf), X2 = ssf * stf;
   const float Y0 = -spf * ssf - csf * cpf * ctf, Y1 = cpf * ssf - csf * spf * ctf, Y2 = stf * csf;
   const float mcs = mc.h * (float)kMsunS;
-  const float K = (float)kAmp0 * sqrtf(mcs) * cbrtf(mcs) * (float)(kC / kMpcM) / dl;
+  // K scaled by 2^70: K P ~ 1e-21 and (K P)^2 would leave FP32's normal range
+  const float K = ldexpf((float)kAmp0 * sqrtf(mcs) * cbrtf(mcs) * (float)(kC / kMpcM) / dl, kKpScaleExp);
   const float ap = 0.5f * (1.0f + ci * ci);
-  double hh = 0.0;
+  float hh = 0.0f;
   for (int det = 0; det < ev.n_det; ++det) {
     const float* xa = ev.xarm32[det];
     const float* ya = ev.yarm32[det];
@@ -163,8 +164,8 @@ __device__ inline void taylorf2_setup_ff(const EventDev& ev, const double* u, Wa
     float yX = ya[0] * X0 + ya[1] * X1 + ya[2] * X2, yY = ya[0] * Y0 + ya[1] * Y1 + ya[2] * Y2;
     float fp = 0.5f * (xX * xX - xY * xY - yX * yX + yY * yY);
     float fc = xX * xY - yX * yY;
-    p.kp_re[det] = (double)(K * (fp * ap));
-    p.kp_im[det] = (double)(K * (-fc * ci));
+    p.kpf_re[det] = K * (fp * ap);
+    p.kpf_im[det] = K * (-fc * ci);
     // tau = t_c - (r . n) / c, and its products with f_min (reduced) and df (split at a 9-bit head)
     const ff dot = ff_add(ff_add(ff_mul(ff_of(ev.vc_f[det][0]), n0), ff_mul(ff_of(ev.vc_f[det][1]), n1)),
                           ff_mul(ff_of(ev.vc_f[det][2]), n2));
@@ -175,10 +176,11 @@ __device__ inline void taylorf2_setup_ff(const EventDev& ev, const double* u, Wa
     const float bh = __int_as_float(__float_as_int(b.h) & (int)0xFFFF8000u);
     p.sbh[det] = bh;
     p.sbl[det] = (b.h - bh) + b.l;
-    const double psum = p.k_end > 0 ? ev.hh_prefix[(size_t)det * ev.n_bins + p.k_end - 1] : 0.0;
-    hh += (p.kp_re[det] * p.kp_re[det] + p.kp_im[det] * p.kp_im[det]) * psum;
+    // <h|h>_det = (K P)^2 sum_{k < k_end} 4 df f^-7/3 / S, with the two 2^(+-140) scalings
+    const float psum = p.k_end > 0 ? ev.hhp32[(size_t)det * ev.n_bins + p.k_end - 1] : 0.0f;
+    hh += (p.kpf_re[det] * p.kpf_re[det] + p.kpf_im[det] * p.kpf_im[det]) * psum;
   }
-  p.hh = hh;
+  p.hh_f = hh;
 }
 
 }  // namespace gwns

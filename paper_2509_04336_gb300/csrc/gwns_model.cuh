@@ -83,6 +83,8 @@ struct EventDev {
   double gw32_unscale;
   // float-float copies of the geometry for the float-float proposal setup
   int ff_setup;                        // 1 when every sampled prior has a float-float transform
+  float dd_f[2];                       // sum_det <d|d> as a float pair
+  const float* hhp32;                  // [n_det][n_bins] hh_prefix * 2^-140 (FP32 range)
   float vc_f[kMaxDet][3][2];           // detector vertex / c [s]
   float fmin_f[2], df_f[2], gmst_f[2];
 };
@@ -114,8 +116,12 @@ struct WalkerParams {
   float ph0h, ph0l;                    // phase0 = ph0h + ph0l
   float sa[kMaxDet];                   // frac(tau f_min)                       [cycles]
   float sbh[kMaxDet], sbl[kMaxDet];    // tau df = sbh + sbl, sbh with 9 significant bits
+  float kpf_re[kMaxDet], kpf_im[kMaxDet];   // K P_det * 2^70 (FP32 range), float-float assembly
+  float hh_f;                          // <h|h> (TaylorF2), float-float assembly
   PhenomExtra pd;                      // IMRPhenomD-form regions (unused for TaylorF2)
 };
+
+constexpr int kKpScaleExp = 70;        // K P ~ 1e-21: scaled by 2^70 into FP32's comfortable range
 
 // ---------------------------------------------------------------- Philox4x64-10
 // Salmon, Moraes, Dror & Shaw 2011: 10 rounds of multiply-xor with a Weyl key schedule.
@@ -327,7 +333,10 @@ __device__ inline void make_ff(const EventDev& ev, WalkerParams& p) {
     e.ph0_mr_h = h;
     e.ph0_mr_l = (float)(e.ph0_mr - (double)h);
   }
+  p.hh_f = (float)p.hh;
   for (int det = 0; det < ev.n_det; ++det) {
+    p.kpf_re[det] = (float)ldexp(p.kp_re[det], kKpScaleExp);
+    p.kpf_im[det] = (float)ldexp(p.kp_im[det], kKpScaleExp);
     double a = p.tau[det] * ev.f_min;
     p.sa[det] = (float)(a - rint(a));
     double b = p.tau[det] * ev.df;

@@ -203,6 +203,14 @@ __device__ inline void cta_sums(const EventDev& ev, const WalkerParams& P, doubl
 template <int PREC, int NDET, int WF>
 __device__ inline double lnl_from_vals(const EventDev& ev, const WalkerParams& P, const double* v) {
   constexpr int NW = (WF == 1 ? 3 : 2);
+  if (PREC == 2 && WF == 0) {   // the float-float path's scaled FP32 amplitudes
+    double dh = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) dh += (double)P.kpf_re[d] * v[NW * d] - (double)P.kpf_im[d] * v[NW * d + 1];
+    dh = ldexp(dh, -kKpScaleExp);
+    const double hh = (double)P.hh_f;
+    return ev.use_ratio ? dh - 0.5 * hh : -0.5 * (ev.dd_total - 2.0 * dh + hh);
+  }
   double sr[kMaxDet], si[kMaxDet], sh[kMaxDet];
   const double hscale = PREC == 0 ? 1.0 : ev.gw32_unscale;
 #pragma unroll
@@ -212,6 +220,28 @@ __device__ inline double lnl_from_vals(const EventDev& ev, const WalkerParams& P
     sh[d] = (WF == 1) ? v[NW * d + 2] * hscale : 0.0;
   }
   return assemble_lnl(ev, P, sr, si, WF == 1 ? sh : nullptr);
+}
+
+// ln L of the float-float TaylorF2 path in float-float arithmetic from the compensated
+// per-detector sums ps = [det][re, im] x (sum, compensation): FP64 only converts the result.
+template <int NDET>
+__device__ inline double lnl_ff(const EventDev& ev, const WalkerParams& P, const float* ps) {
+  ff dh = ff_make(0.0f);
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    const ff sr = fast_two_sum_ff(ps[4 * d], ps[4 * d + 1]);
+    const ff si = fast_two_sum_ff(ps[4 * d + 2], ps[4 * d + 3]);
+    dh = ff_add(dh, ff_sub(ff_mul_f(sr, P.kpf_re[d]), ff_mul_f(si, P.kpf_im[d])));
+  }
+  dh = ff_ldexp(dh, -kKpScaleExp);
+  ff l;
+  if (ev.use_ratio) {
+    l = ff_add_f(dh, -0.5f * P.hh_f);
+  } else {
+    l = ff_add_f(ff_sub(ff_ldexp(dh, 1), ff{ev.dd_f[0], ev.dd_f[1]}), -P.hh_f);
+    l = ff_ldexp(l, -1);
+  }
+  return (double)l.h + (double)l.l;
 }
 
 __device__ inline bool theta_ok(const double* th) {
@@ -548,9 +578,15 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
           sc = 1.0;
         } else {
           Philox4 B = philox4x64((uint64_t)st, wid, it, 1ull, T.key0, T.key1);
-          double prod = __dmul_rn(__dmul_rn(__dmul_rn(rand_open_unit(B.v[0]), rand_open_unit(B.v[1])),
-                                            rand_open_unit(B.v[2])), rand_open_unit(B.v[3]));
-          sc = __dmul_rn(de_scale, __dmul_rn(-0.25, log(prod)));
+          if (PREC == 2) {   // float-float logarithm: the FP64 pipe is left to the likelihoods
+            const ff lp = ff_log_uniform_product(B.v);
+            const ff scf = ff_mul(ff_mul_f(lp, -0.25f), ff_from_double(de_scale));
+            sc = (double)scf.h + (double)scf.l;
+          } else {
+            double prod = __dmul_rn(__dmul_rn(__dmul_rn(rand_open_unit(B.v[0]), rand_open_unit(B.v[1])),
+                                              rand_open_unit(B.v[2])), rand_open_unit(B.v[3]));
+            sc = __dmul_rn(de_scale, __dmul_rn(-0.25, log(prod)));
+          }
         }
         const double* ua = T.surv + a * D;
         const double* ub = T.surv + b * D;
@@ -615,10 +651,14 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
       if (PREC != 0) {
         __syncthreads();
         if (warp == sw && lane < nin) {
-          double v[NV];
+          if (PREC == 2 && WF == 0) {
+            lnl_p[lane] = lnl_ff<NDET>(ev, P[lane], part_sums[lane]);
+          } else {
+            double v[NV];
 #pragma unroll
-          for (int q = 0; q < NV; ++q) v[q] = (double)part_sums[lane][2 * q] + (double)part_sums[lane][2 * q + 1];
-          lnl_p[lane] = lnl_from_vals<PREC, NDET, WF>(ev, P[lane], v);
+            for (int q = 0; q < NV; ++q) v[q] = (double)part_sums[lane][2 * q] + (double)part_sums[lane][2 * q + 1];
+            lnl_p[lane] = lnl_from_vals<PREC, NDET, WF>(ev, P[lane], v);
+          }
         }
       }
     } else {
