@@ -275,6 +275,7 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
   D.gw64 = E.d_gw64;
   D.gw32 = E.d_gw32;
   D.gw32_unscale = 1.0 / gscale;
+  D.hh_unscale_f = (float)std::ldexp(D.gw32_unscale, -2 * kKpScaleExp);
   E.n_dim = nd_dim;
   return NS_OK;
 }

@@ -84,6 +84,7 @@ struct EventDev {
   // float-float copies of the geometry for the float-float proposal setup
   int ff_setup;                        // 1 when every sampled prior has a float-float transform
   float dd_f[2];                       // sum_det <d|d> as a float pair
+  float hh_unscale_f;                  // gw32_unscale * 2^-140 (IMRPhenomD template power, FP32)
   const float* hhp32;                  // [n_det][n_bins] hh_prefix * 2^-140 (FP32 range)
   float vc_f[kMaxDet][3][2];           // detector vertex / c [s]
   float fmin_f[2], df_f[2], gmst_f[2];

@@ -203,12 +203,16 @@ __device__ inline void cta_sums(const EventDev& ev, const WalkerParams& P, doubl
 template <int PREC, int NDET, int WF>
 __device__ inline double lnl_from_vals(const EventDev& ev, const WalkerParams& P, const double* v) {
   constexpr int NW = (WF == 1 ? 3 : 2);
-  if (PREC == 2 && WF == 0) {   // the float-float path's scaled FP32 amplitudes
-    double dh = 0.0;
+  if (PREC == 2) {   // the float-float path's scaled FP32 amplitudes
+    double dh = 0.0, hh = (double)P.hh_f;
 #pragma unroll
-    for (int d = 0; d < NDET; ++d) dh += (double)P.kpf_re[d] * v[NW * d] - (double)P.kpf_im[d] * v[NW * d + 1];
+    for (int d = 0; d < NDET; ++d) {
+      dh += (double)P.kpf_re[d] * v[NW * d] - (double)P.kpf_im[d] * v[NW * d + 1];
+      if (WF == 1)
+        hh += ((double)P.kpf_re[d] * P.kpf_re[d] + (double)P.kpf_im[d] * P.kpf_im[d]) * v[NW * d + 2] *
+              (double)ev.hh_unscale_f;
+    }
     dh = ldexp(dh, -kKpScaleExp);
-    const double hh = (double)P.hh_f;
     return ev.use_ratio ? dh - 0.5 * hh : -0.5 * (ev.dd_total - 2.0 * dh + hh);
   }
   double sr[kMaxDet], si[kMaxDet], sh[kMaxDet];
@@ -224,21 +228,25 @@ __device__ inline double lnl_from_vals(const EventDev& ev, const WalkerParams& P
 
 // ln L of the float-float TaylorF2 path in float-float arithmetic from the compensated
 // per-detector sums ps = [det][re, im] x (sum, compensation): FP64 only converts the result.
-template <int NDET>
+template <int NDET, int WF>
 __device__ inline double lnl_ff(const EventDev& ev, const WalkerParams& P, const float* ps) {
+  constexpr int NS = (WF == 1 ? 6 : 4);   // floats per detector: (re, im(, hh)) x (sum, compensation)
   ff dh = ff_make(0.0f);
+  float hh = P.hh_f;
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
-    const ff sr = fast_two_sum_ff(ps[4 * d], ps[4 * d + 1]);
-    const ff si = fast_two_sum_ff(ps[4 * d + 2], ps[4 * d + 3]);
+    const ff sr = fast_two_sum_ff(ps[NS * d], ps[NS * d + 1]);
+    const ff si = fast_two_sum_ff(ps[NS * d + 2], ps[NS * d + 3]);
     dh = ff_add(dh, ff_sub(ff_mul_f(sr, P.kpf_re[d]), ff_mul_f(si, P.kpf_im[d])));
+    if (WF == 1)
+      hh += (P.kpf_re[d] * P.kpf_re[d] + P.kpf_im[d] * P.kpf_im[d]) * ((ps[NS * d + 4] + ps[NS * d + 5]) * ev.hh_unscale_f);
   }
   dh = ff_ldexp(dh, -kKpScaleExp);
   ff l;
   if (ev.use_ratio) {
-    l = ff_add_f(dh, -0.5f * P.hh_f);
+    l = ff_add_f(dh, -0.5f * hh);
   } else {
-    l = ff_add_f(ff_sub(ff_ldexp(dh, 1), ff{ev.dd_f[0], ev.dd_f[1]}), -P.hh_f);
+    l = ff_add_f(ff_sub(ff_ldexp(dh, 1), ff{ev.dd_f[0], ev.dd_f[1]}), -hh);
     l = ff_ldexp(l, -1);
   }
   return (double)l.h + (double)l.l;
@@ -257,8 +265,9 @@ __device__ inline void setup_from_unit(const EventDev& ev, const double* u, Walk
     double th[kParams], ci, sd, cd;
     unit_to_theta(ev, u, th, &ci, &sd, &cd);
     taylorf2_setup<WF>(ev, th, ci, sd, cd, P);
-  } else if (PREC == 2 && WF == 0 && ev.ff_setup) {
-    taylorf2_setup_ff(ev, u, P);
+  } else if (PREC == 2 && ev.ff_setup) {
+    if (WF == 0) taylorf2_setup_ff(ev, u, P);
+    else phenomd_setup_ff(ev, u, P);
   } else {
     LeanTheta t;
     unit_to_lean(ev, u, t);
@@ -651,8 +660,8 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
       if (PREC != 0) {
         __syncthreads();
         if (warp == sw && lane < nin) {
-          if (PREC == 2 && WF == 0) {
-            lnl_p[lane] = lnl_ff<NDET>(ev, P[lane], part_sums[lane]);
+          if (PREC == 2) {
+            lnl_p[lane] = lnl_ff<NDET, WF>(ev, P[lane], part_sums[lane]);
           } else {
             double v[NV];
 #pragma unroll
