@@ -253,6 +253,7 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
     split(q.cosv, q.cv_f);
     split(q.sinv, q.sv_f);
     q.einv_f = q.e != 0.0 ? (float)(1.0 / q.e) : 0.0f;
+    D.param_dim[i] = p.kind != NS_PRIOR_FIXED ? nd_dim : -1;
     if (p.kind != NS_PRIOR_FIXED) D.dim_param[nd_dim++] = i;
   }
   // the float-float setup transforms uniform priors, the power law of the distance, the sine

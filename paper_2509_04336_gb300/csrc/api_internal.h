@@ -30,7 +30,7 @@ struct NsState {
   double* live_u;      // [n_live][D]
   double* live_lnl;    // [n_live]
   double* surv_u;      // [n_live - k][D]
-  float* surv32;       // [n_live - k][D] FP32 copy for the walk's candidate screen
+  float2* survf;       // [n_live - k][D] float-float copy (h, l) of surv_u
   double* w_u0;        // [k][D]
   double* w_lnl0;      // [k]
   double* w_uo;        // [k][D]

@@ -138,8 +138,10 @@ __device__ __forceinline__ ff ff_log_uniform_product(const uint64_t* x) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const uint64_t m2 = ((x[i] >> 12) << 1) | 1ull;        // 2 (x >> 12) + 1 < 2^53
-    const uint64_t hi = m2 & ~((1ull << 29) - 1ull);        // top 24 bits: exact in a float
-    ff u = fast_two_sum_ff((float)hi, (float)(m2 - hi));
+    // top 24 bits (exact in a float) and the low 29 bits, each converted from 32 bits
+    const float hi = __uint2float_rn((uint32_t)(m2 >> 29)) * 536870912.0f;
+    const float lo = __uint2float_rn((uint32_t)(m2 & ((1ull << 29) - 1ull)));
+    ff u = fast_two_sum_ff(hi, lo);
     int e;
     frexpf(u.h, &e);
     u = ff_ldexp(u, -e);                                    // u in [0.5, 1)

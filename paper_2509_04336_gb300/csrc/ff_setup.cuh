@@ -3,11 +3,11 @@
 //
 // It computes what taylorf2_setup_lean followed by make_ff computes -- prior transform, masses,
 // the 3.5PN phase coefficients regrouped on the frequency basis, the phase constant, the
-// arrival delays and the split time shifts, the antenna patterns and the template power -- but
-// keeps FP64 only for splitting the unit-cube coordinates (FP64 inputs) into float pairs.  With about 48
-// significant bits every coefficient is accurate far below what the phase needs (~1e-6 cycle).
-// The amplitude factors K P_det are FP32, scaled by 2^70, and <h|h> comes from an FP32 copy of
-// the template-power prefix sums scaled by 2^-140; lnl_ff assembles ln L in float-float.
+// arrival delays and the split time shifts, the antenna patterns and the template power -- from
+// the unit-cube coordinates as float pairs, without FP64.  With about 48 significant bits every
+// coefficient is accurate far below what the phase needs (~1e-6 cycle).  The amplitude factors
+// K P_det are FP32, scaled by 2^70, and <h|h> comes from an FP32 copy of the template-power
+// prefix sums scaled by 2^-140; lnl_ff assembles ln L in float-float.
 #pragma once
 
 #include "ff.cuh"
@@ -34,64 +34,77 @@ struct FFCore {
   float dl, ci, psi;
 };
 
-// Prior transform, masses and the 3.5PN coefficients (the same polynomials as
-// taylorf2_pn_coeffs) from the unit-cube point u (requires ev.ff_setup).
-__device__ inline void ff_core(const EventDev& ev, const double* u, FFCore& c) {
-  ff x[kParams];
-  float dl = 1.0f, ci = 1.0f;
-  ff sd = ff_make(0.0f), cd = ff_make(1.0f);
-  int d = 0;
-#pragma unroll 1
-  for (int i = 0; i < kParams; ++i) {
-    const PriorDev& P = ev.prior[i];
-    x[i] = ff_of(P.v_f);
-    if (P.kind == kFixed) {
-      if (i == 4) dl = P.v_f[0];
-      if (i == 5) ci = P.cv_f[0];
-      if (i == 10) { sd = ff_of(P.sv_f); cd = ff_of(P.cv_f); }
-      continue;
-    }
-    const double v = u[d++];
-    if (P.kind == kUniform) {
-      x[i] = ff_add(ff_of(P.lo_f), ff_mul(ff_from_double(v), ff_of(P.w_f)));
-      if (i == 4) dl = x[i].h;
-      if (i == 5) ci = cosf(x[i].h);
-    } else if (P.kind == kPowerLaw) {   // the distance: an amplitude-only parameter
-      dl = powf(P.A_f[0] + (float)v * P.B_f[0], P.einv_f);
-    } else if (P.kind == kSine) {       // cos(theta_jn), amplitude only
-      ci = fminf(1.0f, fmaxf(-1.0f, P.A_f[0] - (float)v * P.B_f[0]));
-    } else {                            // sin(declination)
-      sd = ff_add(ff_of(P.A_f), ff_mul(ff_from_double(v), ff_of(P.B_f)));
-      if (sd.h > 1.0f) sd = ff_make(1.0f);
-      if (sd.h < -1.0f) sd = ff_make(-1.0f);
-      cd = ff_sqrt(ff_mul(ff_add_f(ff_neg(sd), 1.0f), ff_add_f(sd, 1.0f)));
-    }
+// Parameter i with a uniform or fixed prior at the float-float unit-cube point x.
+__device__ __forceinline__ ff ff_prior_lin(const EventDev& ev, int i, const ff* x) {
+  const PriorDev& P = ev.prior[i];
+  const int d = ev.param_dim[i];
+  if (d < 0) return ff_of(P.v_f);
+  return ff_add(ff_of(P.lo_f), ff_mul(x[d], ff_of(P.w_f)));
+}
+// The distance (uniform, power law or fixed): an amplitude-only parameter, FP32.
+__device__ __forceinline__ float ff_prior_dl(const EventDev& ev, const ff* x) {
+  const PriorDev& P = ev.prior[4];
+  const int d = ev.param_dim[4];
+  if (d < 0) return P.v_f[0];
+  if (P.kind == kPowerLaw) return powf(P.A_f[0] + x[d].h * P.B_f[0], P.einv_f);
+  return ff_add(ff_of(P.lo_f), ff_mul(x[d], ff_of(P.w_f))).h;
+}
+// cos(theta_jn) (uniform, sine or fixed prior): amplitude only, FP32.
+__device__ __forceinline__ float ff_prior_ci(const EventDev& ev, const ff* x) {
+  const PriorDev& P = ev.prior[5];
+  const int d = ev.param_dim[5];
+  if (d < 0) return P.cv_f[0];
+  if (P.kind == kSine) return fminf(1.0f, fmaxf(-1.0f, P.A_f[0] - x[d].h * P.B_f[0]));
+  return cosf(ff_add(ff_of(P.lo_f), ff_mul(x[d], ff_of(P.w_f))).h);
+}
+// sin and cos of the declination (uniform, cosine or fixed prior), float-float.
+__device__ __forceinline__ void ff_prior_dec(const EventDev& ev, const ff* x, ff& sd, ff& cd) {
+  const PriorDev& P = ev.prior[10];
+  const int d = ev.param_dim[10];
+  if (d < 0) {
+    sd = ff_of(P.sv_f);
+    cd = ff_of(P.cv_f);
+  } else if (P.kind == kCosine) {
+    sd = ff_add(ff_of(P.A_f), ff_mul(x[d], ff_of(P.B_f)));
+    if (sd.h > 1.0f) sd = ff_make(1.0f);
+    if (sd.h < -1.0f) sd = ff_make(-1.0f);
+    cd = ff_sqrt(ff_mul(ff_add_f(ff_neg(sd), 1.0f), ff_add_f(sd, 1.0f)));
+  } else {
+    ff_sincos(ff_add(ff_of(P.lo_f), ff_mul(x[d], ff_of(P.w_f))), sd, cd);
   }
-  if (ev.prior[10].kind == kUniform) ff_sincos(x[10], sd, cd);
-  c.mc = x[0]; c.q = x[1]; c.chi1 = x[2]; c.chi2 = x[3]; c.phic = x[7]; c.tc = x[8]; c.ra = x[9];
-  c.sd = sd; c.cd = cd; c.dl = dl; c.ci = ci; c.psi = x[6].h;
+}
 
-  // masses and spins
-  const ff q = c.q;
-  c.opq = ff_add_f(q, 1.0f);
+// 1 + q, eta = q / (1 + q)^2 and delta = (1 - q) / (1 + q) from c.q.
+__device__ __forceinline__ void ff_mass_ratio(FFCore& c) {
+  c.opq = ff_add_f(c.q, 1.0f);
   const ff r_opq = ff_div(ff_make(1.0f), c.opq);
-  const ff eta = ff_mul(q, ff_mul(r_opq, r_opq));
-  c.eta = eta;
-  c.delta = ff_mul(ff_add_f(ff_neg(q), 1.0f), r_opq);
-  c.chis = ff_ldexp(ff_add(c.chi1, c.chi2), -1);
-  c.chia = ff_ldexp(ff_sub(c.chi1, c.chi2), -1);
-  const ff chis = c.chis, chia = c.chia;
+  c.eta = ff_mul(c.q, ff_mul(r_opq, r_opq));
+  c.delta = ff_mul(ff_add_f(ff_neg(c.q), 1.0f), r_opq);
+}
+// The powers of (pi M)^(1/3) that the phase needs, from c.mc and c.eta.
+__device__ __forceinline__ void ff_mass_scales(FFCore& c) {
   const ff pmc = ff_mul(GWNS_FF(kPi * kMsunS), c.mc);   // pi Mc [s]
   const ff w = ff_rcbrt(pmc);                            // (pi Mc)^(-1/3)
-  const ff z = ff_rfifth(eta);                           // eta^(-1/5)
+  const ff z = ff_rfifth(c.eta);                         // eta^(-1/5)
   c.c1 = ff_mul(ff_mul(pmc, ff_mul(w, w)), z);           // (pi M)^(1/3)
   const ff z2 = ff_mul(z, z);
-  c.ci1 = ff_mul(ff_mul(w, eta), ff_mul(z2, z2));        // (pi M)^(-1/3)
+  c.ci1 = ff_mul(ff_mul(w, c.eta), ff_mul(z2, z2));      // (pi M)^(-1/3)
   c.ci2 = ff_mul(c.ci1, c.ci1);
   c.ci3 = ff_mul(c.ci2, c.ci1);
   c.ci5 = ff_mul(c.ci3, c.ci2);
+}
+// ln(pi M) and the Newtonian prefactor 3 / (256 pi eta), from c.c1, c.opq and c.q.
+__device__ __forceinline__ void ff_log_and_prefactor(FFCore& c) {
+  c.lpm = ff_mul_f(ff_log(c.c1), 3.0f);
+  c.pre = ff_div(ff_mul(GWNS_FF(3.0 / (256.0 * kPi)), ff_mul(c.opq, c.opq)), c.q);
+}
 
-  // 3.5PN aligned-spin coefficients
+// 3.5PN aligned-spin coefficients (the same polynomials as taylorf2_pn_coeffs) from c.eta,
+// c.delta and the spins.
+__device__ inline void ff_pn_coeffs(FFCore& c) {
+  c.chis = ff_ldexp(ff_add(c.chi1, c.chi2), -1);
+  c.chia = ff_ldexp(ff_sub(c.chi1, c.chi2), -1);
+  const ff eta = c.eta, chis = c.chis, chia = c.chia;
   const ff e2 = ff_mul(eta, eta), e3 = ff_mul(e2, eta);
   const ff dchia = ff_mul(c.delta, chia);
   c.a[0] = ff_make(1.0f);
@@ -130,31 +143,67 @@ __device__ inline void ff_core(const EventDev& ev, const double* u, FFCore& c) {
   }
   c.a[7] = a7;
   c.al5 = ff_mul_f(c.a[5], 3.0f);
-  c.lpm = ff_mul_f(ff_log(c.c1), 3.0f);                 // ln(pi M)
-  c.pre = ff_div(ff_mul(GWNS_FF(3.0 / (256.0 * kPi)), ff_mul(c.opq, c.opq)), q);   // 3/(256 pi eta)
 }
 
-// TaylorF2 phase coefficients on the basis and the phase constant (cycles), float-float.
-__device__ inline void ff_tf2_coeffs(const FFCore& c, WalkerParams& p) {
+// The sky and amplitude parameters of the projection.
+__device__ __forceinline__ void ff_extrinsic(const EventDev& ev, const ff* x, FFCore& c) {
+  c.mc = ff_prior_lin(ev, 0, x);
+  c.tc = ff_prior_lin(ev, 8, x);
+  c.ra = ff_prior_lin(ev, 9, x);
+  c.psi = ff_prior_lin(ev, 6, x).h;
+  c.dl = ff_prior_dl(ev, x);
+  c.ci = ff_prior_ci(ev, x);
+  ff_prior_dec(ev, x, c.sd, c.cd);
+}
+
+// Prior transform, masses and the 3.5PN coefficients from the float-float unit-cube point x
+// (requires ev.ff_setup).
+__device__ inline void ff_core(const EventDev& ev, const ff* x, FFCore& c) {
+  ff_extrinsic(ev, x, c);
+  c.q = ff_prior_lin(ev, 1, x);
+  c.chi1 = ff_prior_lin(ev, 2, x);
+  c.chi2 = ff_prior_lin(ev, 3, x);
+  c.phic = ff_prior_lin(ev, 7, x);
+  ff_mass_ratio(c);
+  ff_mass_scales(c);
+  ff_pn_coeffs(c);
+  ff_log_and_prefactor(c);
+}
+
+// The products that make the TaylorF2 basis coefficients (cycles): C_j for j in [j0, j1).
+__device__ inline void ff_tf2_coeff_range(const FFCore& c, int j0, int j1, WalkerParams& p) {
   const ff pre = c.pre, c1 = c.c1;
   const ff al6 = GWNS_FF(-6848.0 / 21.0);
   const ff lpm3 = ff_mul(c.lpm, GWNS_FF(1.0 / 3.0));
-  ff C[kBasis];
-  C[0] = ff_mul(pre, c.ci5);
-  C[1] = ff_mul(ff_mul(pre, c.ci3), c.a[2]);
-  C[2] = ff_mul(ff_mul(pre, c.ci2), c.a[3]);
-  C[3] = ff_mul(ff_mul(pre, c.ci1), c.a[4]);
-  C[4] = ff_mul(ff_mul(pre, c1), ff_add(c.a[6], ff_mul(al6, lpm3)));
-  C[5] = ff_mul(ff_mul(pre, ff_mul(c1, c1)), c.a[7]);
-  C[6] = ff_mul(ff_mul(pre, c.al5), GWNS_FF(1.0 / 3.0));
-  C[7] = ff_mul(ff_mul(ff_mul(pre, c1), al6), GWNS_FF(1.0 / 3.0));
 #pragma unroll
-  for (int j = 0; j < kBasis; ++j) { p.Ch[j] = C[j].h; p.Cl[j] = C[j].l; }
-  ff ph0 = ff_mul(pre, ff_add(c.a[5], ff_mul(c.al5, lpm3)));
+  for (int j = 0; j < kBasis; ++j) {
+    if (j < j0 || j >= j1) continue;
+    ff C;
+    if (j == 0) C = ff_mul(pre, c.ci5);
+    else if (j == 1) C = ff_mul(ff_mul(pre, c.ci3), c.a[2]);
+    else if (j == 2) C = ff_mul(ff_mul(pre, c.ci2), c.a[3]);
+    else if (j == 3) C = ff_mul(ff_mul(pre, c.ci1), c.a[4]);
+    else if (j == 4) C = ff_mul(ff_mul(pre, c1), ff_add(c.a[6], ff_mul(al6, lpm3)));
+    else if (j == 5) C = ff_mul(ff_mul(pre, ff_mul(c1, c1)), c.a[7]);
+    else if (j == 6) C = ff_mul(ff_mul(pre, c.al5), GWNS_FF(1.0 / 3.0));
+    else C = ff_mul(ff_mul(ff_mul(pre, c1), al6), GWNS_FF(1.0 / 3.0));
+    p.Ch[j] = C.h;
+    p.Cl[j] = C.l;
+  }
+}
+// The phase constant (cycles).
+__device__ inline void ff_tf2_phase0(const FFCore& c, WalkerParams& p) {
+  const ff lpm3 = ff_mul(c.lpm, GWNS_FF(1.0 / 3.0));
+  ff ph0 = ff_mul(c.pre, ff_add(c.a[5], ff_mul(c.al5, lpm3)));
   ph0 = ff_sub(ph0, ff_mul(c.phic, GWNS_FF(1.0 / kPi)));
   ph0 = ff_add_f(ph0, -0.125f);
   p.ph0h = ph0.h;
   p.ph0l = ph0.l;
+}
+// TaylorF2 phase coefficients on the basis and the phase constant, float-float.
+__device__ inline void ff_tf2_coeffs(const FFCore& c, WalkerParams& p) {
+  ff_tf2_coeff_range(c, 0, kBasis, p);
+  ff_tf2_phase0(c, p);
 }
 
 // Number of bins with f_k <= f_cut (le) or f_k < f_cut (strict), float-float comparisons.
@@ -171,8 +220,8 @@ __device__ inline int ff_bins_below(const EventDev& ev, ff f_cut, bool strict) {
 }
 
 // Sky direction (float-float: it sets the arrival delays), antenna patterns and amplitude in
-// FP32 (K P scaled by 2^70), the split time shifts, and for TaylorF2 <h|h> from the prefix sums.
-__device__ inline void ff_projection(const EventDev& ev, const FFCore& c, WalkerParams& p, bool tf2) {
+// FP32 (K P scaled by 2^70) and the split time shifts.
+__device__ inline void ff_projection(const EventDev& ev, const FFCore& c, WalkerParams& p) {
   ff sp, cp;
   ff_sincos(ff_sub(c.ra, ff_of(ev.gmst_f)), sp, cp);
   const ff n0 = ff_mul(c.cd, cp), n1 = ff_mul(c.cd, sp), n2 = c.sd;
@@ -185,7 +234,6 @@ __device__ inline void ff_projection(const EventDev& ev, const FFCore& c, Walker
   // K scaled by 2^70: K P ~ 1e-21 and (K P)^2 would leave FP32's normal range
   const float K = ldexpf((float)kAmp0 * sqrtf(mcs) * cbrtf(mcs) * (float)(kC / kMpcM) / c.dl, kKpScaleExp);
   const float ap = 0.5f * (1.0f + c.ci * c.ci);
-  float hh = 0.0f;
   for (int det = 0; det < ev.n_det; ++det) {
     const float* xa = ev.xarm32[det];
     const float* ya = ev.yarm32[det];
@@ -205,23 +253,85 @@ __device__ inline void ff_projection(const EventDev& ev, const FFCore& c, Walker
     const float bh = __int_as_float(__float_as_int(b.h) & (int)0xFFFF8000u);
     p.sbh[det] = bh;
     p.sbl[det] = (b.h - bh) + b.l;
-    if (tf2) {
-      // <h|h>_det = (K P)^2 sum_{k < k_end} 4 df f^-7/3 / S, with the two 2^(+-140) scalings
-      const float psum = p.k_end > 0 ? ev.hhp32[(size_t)det * ev.n_bins + p.k_end - 1] : 0.0f;
-      hh += (p.kpf_re[det] * p.kpf_re[det] + p.kpf_im[det] * p.kpf_im[det]) * psum;
-    }
+  }
+}
+
+// TaylorF2 <h|h> = sum_det (K P_det)^2 sum_{k < k_end} 4 df f^-7/3 / S from the prefix sums
+// (the two 2^(+-140) scalings cancel in the assembly); needs p.k_end and p.kpf.
+__device__ inline void ff_tf2_hh(const EventDev& ev, WalkerParams& p) {
+  float hh = 0.0f;
+  for (int det = 0; det < ev.n_det; ++det) {
+    const float psum = p.k_end > 0 ? ev.hhp32[(size_t)det * ev.n_bins + p.k_end - 1] : 0.0f;
+    hh += (p.kpf_re[det] * p.kpf_re[det] + p.kpf_im[det] * p.kpf_im[det]) * psum;
   }
   p.hh_f = hh;
 }
 
-// Mode-2 TaylorF2 proposal constants straight from the unit-cube point u.
-__device__ inline void taylorf2_setup_ff(const EventDev& ev, const double* u, WalkerParams& p) {
+// Last bin at or below the test-mass ISCO frequency 1/(6^(3/2) pi M).
+__device__ __forceinline__ int ff_tf2_kend(const EventDev& ev, const FFCore& c) {
+  return ff_bins_below(ev, ff_mul(GWNS_FF(1.0 / kSix15), c.ci3), false);
+}
+
+// Mode-2 TaylorF2 proposal constants straight from the float-float unit-cube point x.
+__device__ inline void taylorf2_setup_ff(const EventDev& ev, const ff* x, WalkerParams& p) {
   FFCore c;
-  ff_core(ev, u, c);
-  // last bin at or below the test-mass ISCO frequency 1/(6^(3/2) pi M)
-  p.k_end = ff_bins_below(ev, ff_mul(GWNS_FF(1.0 / kSix15), c.ci3), false);
+  ff_core(ev, x, c);
+  p.k_end = ff_tf2_kend(ev, c);
   ff_tf2_coeffs(c, p);
-  ff_projection(ev, c, p, true);
+  ff_projection(ev, c, p);
+  ff_tf2_hh(ev, p);
+}
+
+// The same constants formed by the warps of a CTA at once: each warp runs one part for every
+// proposal of a round (lane i: proposal i), the parts exchange through shared memory, then a
+// second pass forms the products.  The arithmetic is the one-lane setup's, split at its
+// independent chains -- first pass: (0) mass scales, ln(pi M), prefactor; (1) PN coefficients;
+// (2) sky, antenna patterns, delays; second pass: (0, 1) the basis coefficients, (2) the phase
+// constant, (3) the ISCO bin and <h|h>.  TF2Part carries (0) and (1) to the second pass.
+struct TF2Part {
+  ff pre, c1, ci1, ci2, ci3, ci5, lpm, phic;
+  ff a[8], al5;
+};
+
+__device__ inline void tf2_split_first(int part, const EventDev& ev, const ff* x, TF2Part& s, WalkerParams& p) {
+  FFCore c;
+  if (part == 0) {
+    c.mc = ff_prior_lin(ev, 0, x);
+    c.q = ff_prior_lin(ev, 1, x);
+    ff_mass_ratio(c);
+    ff_mass_scales(c);
+    ff_log_and_prefactor(c);
+    s.pre = c.pre; s.c1 = c.c1; s.ci1 = c.ci1; s.ci2 = c.ci2; s.ci3 = c.ci3; s.ci5 = c.ci5; s.lpm = c.lpm;
+    s.phic = ff_prior_lin(ev, 7, x);
+  } else if (part == 1) {
+    c.q = ff_prior_lin(ev, 1, x);
+    c.chi1 = ff_prior_lin(ev, 2, x);
+    c.chi2 = ff_prior_lin(ev, 3, x);
+    ff_mass_ratio(c);
+    ff_pn_coeffs(c);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s.a[j] = c.a[j];
+    s.al5 = c.al5;
+  } else if (part == 2) {
+    ff_extrinsic(ev, x, c);
+    ff_projection(ev, c, p);
+  }
+}
+
+__device__ inline void tf2_split_second(int part, const EventDev& ev, const TF2Part& s, WalkerParams& p) {
+  FFCore c;
+  c.pre = s.pre; c.c1 = s.c1; c.ci1 = s.ci1; c.ci2 = s.ci2; c.ci3 = s.ci3; c.ci5 = s.ci5; c.lpm = s.lpm;
+  c.phic = s.phic;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) c.a[j] = s.a[j];
+  c.al5 = s.al5;
+  if (part == 0) ff_tf2_coeff_range(c, 0, 4, p);
+  else if (part == 1) ff_tf2_coeff_range(c, 4, 8, p);
+  else if (part == 2) ff_tf2_phase0(c, p);
+  else {
+    p.k_end = ff_tf2_kend(ev, c);
+    ff_tf2_hh(ev, p);
+  }
 }
 
 // Mode-2 IMRPhenomD-form proposal constants from the unit-cube point u: the TaylorF2 part as
@@ -229,9 +339,9 @@ __device__ inline void taylorf2_setup_ff(const EventDev& ev, const double* u, Wa
 // continuity constants and the region coefficients in float-float, the bin boundaries by
 // float-float comparisons, the ringdown frequency, damping and amplitude shape in FP32 (the
 // FP64 path's FAST variant rounds the same quantities to FP32).
-__device__ inline void phenomd_setup_ff(const EventDev& ev, const double* u, WalkerParams& p) {
+__device__ inline void phenomd_setup_ff(const EventDev& ev, const ff* x, WalkerParams& p) {
   FFCore c;
-  ff_core(ev, u, c);
+  ff_core(ev, x, c);
   ff_tf2_coeffs(c, p);
   PhenomExtra& e = p.pd;
   const ff eta = c.eta;
@@ -341,7 +451,8 @@ __device__ inline void phenomd_setup_ff(const EventDev& ev, const double* u, Wal
   e.hc3f = 2.0f * (y0 - y1) + span * d0 + span * d1;
   e.frdf = frd; e.gdf = gd; e.g1gdf = (float)kPdG1 * gd; e.g2_gdf = (float)kPdG2 / gd;
   e.at_scalef = (float)kPdA4 * (inv2pe.h + inv2pe.l); e.at_cf = (float)kPdA5 * frd; e.at_invf = 1.0f / fd;
-  ff_projection(ev, c, p, false);
+  ff_projection(ev, c, p);
+  p.hh_f = 0.0f;   // the IMRPhenomD form sums its template power per bin
 }
 
 }  // namespace gwns

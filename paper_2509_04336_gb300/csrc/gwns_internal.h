@@ -15,7 +15,7 @@ constexpr int kThreads = 128;   // threads per walker CTA
 // replays without host involvement.
 struct WalkTask {
   const double* surv;      // [n_s][D] survivors
-  const float* surv32;     // [n_s][D] FP32 copy used only to screen candidates (may be null)
+  const float2* survf;     // [n_s][D] float-float copy (h, l) of surv (may be null)
   const double* u0;        // [n][D] starts
   const double* lnl0;      // [n]
   double* u_out;           // [n][D]

@@ -72,6 +72,7 @@ struct EventDev {
   float xarm32[kMaxDet][3], yarm32[kMaxDet][3];
   PriorDev prior[kParams];
   int dim_param[kMaxDim];              // physical index of each sampled dimension
+  int param_dim[kParams];              // sampled dimension of each parameter (-1: fixed)
   const double* basis64;               // [n_bins][kBasis]
   const float2* basis_ff;              // [n_bins][kBasis] (hi, lo) float-float copy of basis64
   const double2* z64;                  // [n_det][n_bins]

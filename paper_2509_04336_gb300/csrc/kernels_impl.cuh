@@ -266,8 +266,11 @@ __device__ inline void setup_from_unit(const EventDev& ev, const double* u, Walk
     unit_to_theta(ev, u, th, &ci, &sd, &cd);
     taylorf2_setup<WF>(ev, th, ci, sd, cd, P);
   } else if (PREC == 2 && ev.ff_setup) {
-    if (WF == 0) taylorf2_setup_ff(ev, u, P);
-    else phenomd_setup_ff(ev, u, P);
+    ff x[kMaxDim];
+#pragma unroll
+    for (int d = 0; d < kMaxDim; ++d) x[d] = d < ev.n_dim ? ff_from_double(u[d]) : ff_make(0.0f);
+    if (WF == 0) taylorf2_setup_ff(ev, x, P);
+    else phenomd_setup_ff(ev, x, P);
   } else {
     LeanTheta t;
     unit_to_lean(ev, u, t);
@@ -522,13 +525,13 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
       // 1e-5 (1 + |s|) never rejects a step that the exact FP64 test accepts
       const float margin = 1e-5f * (1.0f + fabsf(sc));
       maybe = 1;
-      if (T.surv32) {
-        const float* ua = T.surv32 + a * D;
-        const float* ub = T.surv32 + b * D;
+      if (T.survf) {
+        const float2* ua = T.survf + a * D;
+        const float2* ub = T.survf + b * D;
 #pragma unroll
         for (int d = 0; d < kMaxDim; ++d) {
           if (d < D && !ev.prior[ev.dim_param[d]].periodic) {
-            float x = u32[d] + sc * (ua[d] - ub[d]);
+            float x = u32[d] + sc * (ua[d].x - ub[d].x);
             if (!(x >= -margin && x <= 1.0f + margin)) maybe = 0;
           }
         }
@@ -718,6 +721,289 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
   }
 }
 
+// ---------------------------------------------------------------- float-float walk (mode 2)
+__device__ __forceinline__ bool ff_in_unit(ff x) {
+  // x normalised (|l| <= ulp(h) / 2, so h = 0 implies l = 0); NaN fails the first test
+  return x.h >= 0.0f && (x.h < 1.0f || (x.h == 1.0f && x.l <= 0.0f));
+}
+// x - floor(x) of a float-float value (the periodic dimensions).
+__device__ __forceinline__ ff ff_wrap_unit(ff x) {
+  float fl = floorf(x.h);
+  if (x.h == fl && x.l < 0.0f) fl -= 1.0f;
+  return ff_add_f(x, -fl);
+}
+
+// The acceptance walk of mode 2.  The round of walk_kernel, restructured so that its serial
+// part is short:
+//  1. every thread forms the move of one candidate step of the window exactly, in float-float
+//     arithmetic (the DE scale's logarithm, the survivors' float-float difference, the periodic
+//     wrap, the bounds test) -- there is no FP32 screen and no one-warp recheck -- and a ballot
+//     compacts the first m in-bounds moves;
+//  2. the TaylorF2 setup of the round runs on all four warps at once (tf2_split_first /
+//     tf2_split_second: four independent chains, then the products); the IMRPhenomD-form
+//     setup, a small part of its round, stays on one rotating warp;
+//  3. the likelihoods, one warp per proposal (the whole CTA per proposal when m < 4);
+//  4. warp 0 assembles ln L of every proposal in float-float and finds the first acceptance
+//     with one ballot.
+// The DE move is the walk's, u' = u + gamma (u_a - u_b), with the position and the survivors as
+// float pairs (~48 significant bits): the chain is the FP64 chain up to rounding at ~1e-14.
+// A round of three or more proposals is padded to a multiple of four: the likelihood phase
+// takes as long for 5 proposals as for 8, and the padding only advances the chain further.
+template <int NDET, int WF>
+__global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __restrict__ evs, WalkTask* tasks,
+                                                            const int32_t* __restrict__ blk_task,
+                                                            const int32_t* __restrict__ blk_local) {
+  constexpr int NV = NVals<NDET, WF>::value;
+  __shared__ WalkerParams P[kSpecMax];
+  __shared__ ff propf[kSpecMax][kMaxDim];
+  __shared__ TF2Part parts[WF == 0 ? kSpecMax : 1];
+  __shared__ int cstep[kSpecMax];
+  __shared__ double lnl_p[kSpecMax];
+  __shared__ float part_sums[kSpecMax][2 * kMaxVals];
+  __shared__ double u[kMaxDim];
+  __shared__ ff uf[kMaxDim];
+  __shared__ double red[kWarps][kMaxVals];
+  __shared__ double vals[kMaxVals];
+  __shared__ int wcount[kWarps];
+  __shared__ int s_next, s_setup_warp, s_end, s_needq;
+  __shared__ int s_isflow[kSpecMax];
+  __shared__ float s_lqf[kSpecMax];
+  __shared__ float s_logq;
+  __shared__ FlowScratch fscr;
+  const WalkTask& T = tasks[blk_task[blockIdx.x]];
+  const int j = blk_local[blockIdx.x];
+  const EventDev& ev = evs[T.event];
+  if (T.done) return;
+  const int D = ev.n_dim;
+  const int n_steps = T.n_steps;
+  const double lnl_star = T.lnl_star;
+  const uint64_t it = (uint64_t)T.iteration;
+  const uint64_t wid = (uint64_t)(T.walker_offset + j);
+  const uint64_t n_s = (uint64_t)T.n_s;
+  int m = T.spec < 1 ? 1 : (T.spec > kSpecMax ? kSpecMax : T.spec);
+  if (m >= 3) m = min((m + 3) & ~3, kSpecMax);
+  const int window = min(kThreads, max(32, 4 * m));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool split = WF == 0 && ev.ff_setup;
+  if (threadIdx.x < D) {
+    const double v = T.u0[(size_t)j * D + threadIdx.x];
+    u[threadIdx.x] = v;
+    uf[threadIdx.x] = ff_from_double(v);
+  }
+  if (threadIdx.x == 0) {
+    unsigned int smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    s_setup_warp = (int)(atomicAdd(&g_walk_sm_arrivals[smid & 255u], 1u) % (unsigned)kWarps);
+  }
+  unsigned periodic = 0u;
+#pragma unroll
+  for (int d = 0; d < kMaxDim; ++d)
+    if (d < D && ev.prior[ev.dim_param[d]].periodic) periodic |= 1u << d;
+  double lnl = T.lnl0[j];
+  int n_acc = 0, n_like = 0;
+  int64_t n_bins = 0, n_spec = 0;
+  const ff de_scale = ff_from_double(2.38 / sqrt(2.0 * (double)D));
+  __syncthreads();
+  const int sw = s_setup_warp;
+  const bool use_flow = T.flow != nullptr && T.p_flow > 0.0;
+  const double p_flow = T.p_flow;
+  if (use_flow) {
+    const float lq = flow_logq_cta(*T.flow, u, fscr);
+    if (threadIdx.x == 0) s_logq = lq;
+    __syncthreads();
+  }
+  int t = 0;
+  while (t < n_steps) {
+    const int W = min(window, n_steps - t);
+    // 1. the exact move of one candidate step per thread
+    const int step = t + (int)threadIdx.x;
+    int in = 0, isf = 0;
+    float lqf = 0.0f;
+    ff xf[kMaxDim];
+    if ((int)threadIdx.x < W) {
+      // the step's Philox blocks: (tag 6: flow coin,) tag 0: survivors and scale coin,
+      // tag 1: the scale's uniforms -- one inlined generator, called up to three times
+      Philox4 A, B;
+      bool draw_scale = false;
+      int tag = use_flow ? 6 : 0;
+#pragma unroll 1
+      while (tag >= 0) {
+        const Philox4 r = philox4x64((uint64_t)step, wid, it, (uint64_t)tag, T.key0, T.key1);
+        if (tag == 6) {
+          tag = 0;
+          if (rand_open_unit(r.v[0]) < p_flow) {
+            isf = 1;
+            lqf = (float)T.flq[(size_t)j * T.f_stride + step];
+            in = logf((float)rand_open_unit(r.v[1])) < s_logq - lqf;
+            tag = -1;
+          }
+        } else if (tag == 0) {
+          A = r;
+          draw_scale = (r.v[2] >> 63) == 0ull;
+          tag = draw_scale ? 1 : -1;
+        } else {
+          B = r;
+          tag = -1;
+        }
+      }
+      if (isf) {
+        if (in) {
+          const double* fu = T.fu + ((size_t)j * T.f_stride + step) * D;
+#pragma unroll
+          for (int d = 0; d < kMaxDim; ++d)
+            if (d < D) xf[d] = ff_from_double(fu[d]);
+        }
+      } else {
+        const uint64_t a = rand_index(A.v[0], n_s);
+        uint64_t b = rand_index(A.v[1], n_s - 1);
+        b += (b >= a) ? 1ull : 0ull;
+        // both survivors' coordinates first (branch-free, all loads in flight at once)
+        ff ua[kMaxDim], ub[kMaxDim];
+        if (T.survf) {
+#pragma unroll
+          for (int d = 0; d < kMaxDim; ++d) {
+            const int dd = d < D ? d : D - 1;
+            const float2 pa = T.survf[a * D + dd], pb = T.survf[b * D + dd];
+            ua[d] = ff{pa.x, pa.y};
+            ub[d] = ff{pb.x, pb.y};
+          }
+        } else {
+#pragma unroll
+          for (int d = 0; d < kMaxDim; ++d) {
+            const int dd = d < D ? d : D - 1;
+            ua[d] = ff_from_double(T.surv[a * D + dd]);
+            ub[d] = ff_from_double(T.surv[b * D + dd]);
+          }
+        }
+        const ff sc = draw_scale ? ff_mul(ff_mul_f(ff_log_uniform_product(B.v), -0.25f), de_scale) : ff_make(1.0f);
+        in = 1;
+#pragma unroll
+        for (int d = 0; d < kMaxDim; ++d) {
+          ff x = ff_add(uf[d < D ? d : D - 1], ff_mul(sc, ff_sub(ua[d], ub[d])));
+          const ff xw = ff_wrap_unit(x);
+          if ((periodic >> d) & 1u) x = xw;
+          if (d < D && !ff_in_unit(x)) in = 0;
+          xf[d] = x;
+        }
+      }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, in);
+    if (lane == 0) wcount[warp] = __popc(mask);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < kWarps; ++w2) {
+      const int cw = wcount[w2];
+      before += (w2 < warp) ? cw : 0;
+      total += cw;
+    }
+    const int slot = before + __popc(mask & ((1u << lane) - 1u));
+    if (in && slot < m) {
+#pragma unroll
+      for (int d = 0; d < kMaxDim; ++d)
+        if (d < D) propf[slot][d] = xf[d];
+      cstep[slot] = step;
+      s_isflow[slot] = isf;
+      s_lqf[slot] = lqf;
+      // the round covers the steps up to the m-th in-bounds one, else the whole window
+      if (slot == m - 1 && total > m) s_end = step;
+    }
+    if (threadIdx.x == 0 && total <= m) s_end = t + W - 1;
+    const int nin = min(total, m);
+    __syncthreads();
+    // 2. proposal constants
+    if (nin > 0) {
+      if (split) {
+        if (lane < nin) tf2_split_first(warp, ev, propf[lane], parts[lane], P[lane]);
+        __syncthreads();
+        if (lane < nin) tf2_split_second(warp, ev, parts[lane], P[lane]);
+      } else if (warp == sw && lane < nin) {
+        if (ev.ff_setup) {
+          if (WF == 0) taylorf2_setup_ff(ev, propf[lane], P[lane]);
+          else phenomd_setup_ff(ev, propf[lane], P[lane]);
+        } else {
+          double pd[kMaxDim];
+#pragma unroll
+          for (int d = 0; d < kMaxDim; ++d) pd[d] = d < D ? (double)propf[lane][d].h + (double)propf[lane][d].l : 0.0;
+          setup_from_unit<2, WF>(ev, pd, P[lane]);
+        }
+      }
+      __syncthreads();
+    }
+    // 3. likelihoods
+    if (nin >= kWarps) {
+      for (int i = warp; i < nin; i += kWarps) {
+        double dv[NV];
+        float fv[NV], fc[NV];
+        partials<2, NDET, WF>(ev, P[i], lane, 32, dv, fv, fc);
+        float rs, rc;
+        int q;
+        warp_halving_sums<NV>(fv, fc, lane, rs, rc, q);
+        constexpr int V = Pow2Vals<NV>::value;
+        constexpr int group = 32 / V;
+        if ((lane & (group - 1)) == 0 && q < NV) { part_sums[i][2 * q] = rs; part_sums[i][2 * q + 1] = rc; }
+      }
+      __syncthreads();
+    } else {
+      for (int i = 0; i < nin; ++i) {
+        cta_sums<2, NDET, WF>(ev, P[i], red, vals);
+        if (threadIdx.x == 0) lnl_p[i] = lnl_from_vals<2, NDET, WF>(ev, P[i], vals);
+        __syncthreads();
+      }
+    }
+    // 4. ln L of every proposal, then the steps in order: the first acceptance ends the round
+    if (warp == 0) {
+      double l = 0.0;
+      if (lane < nin) l = nin >= kWarps ? lnl_ff<NDET, WF>(ev, P[lane], part_sums[lane]) : lnl_p[lane];
+      const unsigned am = __ballot_sync(0xffffffffu, lane < nin && l > lnl_star);
+      const int c = am ? __ffs(am) - 1 : -1;
+      const int used = c >= 0 ? c + 1 : nin;
+      int kb = lane < used ? P[lane].k_end : 0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) kb += __shfl_xor_sync(0xffffffffu, kb, off);
+      if (c >= 0) {
+        lnl = __shfl_sync(0xffffffffu, l, c);
+        if (lane < D) {
+          const ff x = propf[c][lane];
+          uf[lane] = x;
+          u[lane] = (double)x.h + (double)x.l;
+        }
+      }
+      if (lane == 0) {
+        n_like += used;
+        n_bins += kb;
+        n_spec += nin;
+        int nxt = s_end + 1;
+        s_needq = 0;
+        if (c >= 0) {
+          ++n_acc;
+          nxt = cstep[c] + 1;
+          if (use_flow) {
+            if (s_isflow[c]) s_logq = s_lqf[c];
+            else s_needq = 1;
+          }
+        }
+        s_next = nxt;
+      }
+    }
+    __syncthreads();
+    t = s_next;
+    if (use_flow && s_needq && t < n_steps) {
+      const float lq = flow_logq_cta(*T.flow, u, fscr);
+      if (threadIdx.x == 0) s_logq = lq;
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x < D) T.u_out[(size_t)j * D + threadIdx.x] = u[threadIdx.x];
+  if (threadIdx.x == 0) {
+    T.lnl_out[j] = lnl;
+    T.n_acc[j] = n_acc;
+    T.n_like[j] = n_like;
+    if (T.n_bins) T.n_bins[j] = n_bins;
+    if (T.n_spec) T.n_spec[j] = n_spec;
+  }
+}
+
 }  // namespace
 
 // Launchers of one precision P; each kernels_pP.cu instantiates its own.
@@ -745,11 +1031,18 @@ cudaError_t launch_unit_likelihood_p(int waveform, int n_det, const EventDev* d_
   return cudaGetLastError();
 }
 
+// Mode 2 runs the float-float walk; modes 0 and 1 the FP64-recheck walk.
+template <int P, int N, int W>
+void launch_walk_one(int n_blocks, cudaStream_t s, const EventDev* d_evs, WalkTask* d_tasks,
+                     const int32_t* d_blk_task, const int32_t* d_blk_local) {
+  if constexpr (P == 2) walk_kernel_ff<N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local);
+  else walk_kernel<P, N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local);
+}
+
 template <int P>
 cudaError_t launch_walk_p(int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
                           const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s) {
-#define GWNS_WALK(P_, N, W) \
-  walk_kernel<P_, N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local)
+#define GWNS_WALK(P_, N, W) launch_walk_one<P_, N, W>(n_blocks, s, d_evs, d_tasks, d_blk_task, d_blk_local)
   GWNS_DISPATCH_W(GWNS_WALK, P)
 #undef GWNS_WALK
   return cudaGetLastError();

@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(NsState* states, Wa
     for (int d = 0; d < D; ++d) {
       double v = S.live_u[(size_t)id * D + d];
       S.surv_u[(size_t)i * D + d] = v;
-      S.surv32[(size_t)i * D + d] = (float)v;
+      const float vh = __double2float_rn(v);
+      S.survf[(size_t)i * D + d] = make_float2(vh, __double2float_rn(v - (double)vh));
     }
   }
   const uint64_t it = (uint64_t)S.iteration;
@@ -487,7 +488,7 @@ int nested_init(ns_handle* h) {
     if ((r = alloc(h, (void**)&S.live_u, sizeof(double) * n * D, "live_u")) ||
         (r = alloc(h, (void**)&S.live_lnl, sizeof(double) * n, "live_lnl")) ||
         (r = alloc(h, (void**)&S.surv_u, sizeof(double) * (n - k) * D, "surv_u")) ||
-        (r = alloc(h, (void**)&S.surv32, sizeof(float) * (n - k) * D, "surv32")) ||
+        (r = alloc(h, (void**)&S.survf, sizeof(float2) * (n - k) * D, "survf")) ||
         (r = alloc(h, (void**)&S.w_u0, sizeof(double) * k * D, "w_u0")) ||
         (r = alloc(h, (void**)&S.w_lnl0, sizeof(double) * k, "w_lnl0")) ||
         (r = alloc(h, (void**)&S.w_uo, sizeof(double) * k * D, "w_uo")) ||
@@ -504,7 +505,7 @@ int nested_init(ns_handle* h) {
       return r;
     WalkTask& T = tasks[e];
     std::memset(&T, 0, sizeof(T));
-    T.surv = S.surv_u; T.surv32 = S.surv32; T.u0 = S.w_u0; T.lnl0 = S.w_lnl0; T.u_out = S.w_uo; T.lnl_out = S.w_lo;
+    T.surv = S.surv_u; T.survf = S.survf; T.u0 = S.w_u0; T.lnl0 = S.w_lnl0; T.u_out = S.w_uo; T.lnl_out = S.w_lo;
     T.n_acc = S.w_na; T.n_like = S.w_nl; T.n_bins = S.w_nb; T.n_spec = S.w_ns; T.spec = S.spec;
     T.lnl_star = -INFINITY; T.iteration = 0; T.walker_offset = 0;
     T.key0 = S.key0; T.key1 = S.key1; T.n_s = S.n_live - S.k; T.n = S.k; T.n_steps = S.n_steps;
@@ -547,7 +548,7 @@ void nested_free(ns_handle* h) {
   h->walk_events.clear();
   for (auto& E : h->events) {
     NsState& S = E.ns;
-    void* ptrs[] = {S.live_u, S.live_lnl, S.surv_u, S.surv32, S.w_u0, S.w_lnl0, S.w_uo, S.w_lo, S.w_na, S.w_nl,
+    void* ptrs[] = {S.live_u, S.live_lnl, S.surv_u, S.survf, S.w_u0, S.w_lnl0, S.w_uo, S.w_lo, S.w_na, S.w_nl,
                     S.slot, S.w_nb, S.w_ns, S.dead_u, S.dead_lnl, S.dead_logw, S.dead_nlive};
     for (void* p : ptrs) cudaFree(p);
     std::memset(&S, 0, sizeof(S));
@@ -830,7 +831,7 @@ extern "C" int ns_state_load(ns_handle* h, const char* path) {
   for (int e = 0; e < ne; ++e) {
     NsState S = saved[e];
     const NsState& cur = h->events[e].ns;
-    S.live_u = cur.live_u; S.live_lnl = cur.live_lnl; S.surv_u = cur.surv_u; S.surv32 = cur.surv32;
+    S.live_u = cur.live_u; S.live_lnl = cur.live_lnl; S.surv_u = cur.surv_u; S.survf = cur.survf;
     S.w_u0 = cur.w_u0; S.w_lnl0 = cur.w_lnl0; S.w_uo = cur.w_uo; S.w_lo = cur.w_lo;
     S.w_na = cur.w_na; S.w_nl = cur.w_nl; S.slot = cur.slot;
     S.dead_u = cur.dead_u; S.dead_lnl = cur.dead_lnl; S.dead_logw = cur.dead_logw; S.dead_nlive = cur.dead_nlive;

@@ -47,6 +47,7 @@ def walk_inputs(w, ev, n_surv, n_walk, seed):
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, 2),
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, 32),
     ("bbh11_3det_8s_phenomd", synth.PREC_FP64, 8),
+    ("bbh11_3det_8s_phenomd", synth.PREC_MIXED_FF, 2),
     ("bbh11_3det_8s_phenomd", synth.PREC_MIXED_FF, 16),
 ])
 def test_walk_parity(name, precision, spec):
