@@ -143,7 +143,7 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
     }
     for (int j = 0; j < nbas; ++j) {
       float hi = (float)g[j];
-      basis_ff[(size_t)k * nbas + j] = make_float2(hi, (float)(g[j] - (double)hi));
+      basis_ff[(size_t)j * nb + k] = make_float2(hi, (float)(g[j] - (double)hi));
     }
   }
   for (int d = 0; d < nd; ++d) {

@@ -74,7 +74,8 @@ struct EventDev {
   int dim_param[kMaxDim];              // physical index of each sampled dimension
   int param_dim[kParams];              // sampled dimension of each parameter (-1: fixed)
   const double* basis64;               // [n_bins][kBasis]
-  const float2* basis_ff;              // [n_bins][kBasis] (hi, lo) float-float copy of basis64
+  const float2* basis_ff;              // [n_basis][n_bins] (hi, lo) float-float copy of basis64,
+                                       // term-major: a warp's loads of one term are contiguous
   const double2* z64;                  // [n_det][n_bins]
   const float2* z32;                   // [n_det][n_bins]
   const double* hh_prefix;             // [n_det][n_bins] inclusive prefix sums of 4 df f^-7/3 / S
@@ -563,7 +564,8 @@ __device__ __forceinline__ void bin_accumulate_mixed(const EventDev& ev, const W
 template <int NDET>
 __device__ __forceinline__ void bin_accumulate_ff(const EventDev& ev, const WalkerParams& p, int k,
                                                   AccF32& acc) {
-  const float2* g = ev.basis_ff + (size_t)k * ev.n_basis;
+  const float2* g = ev.basis_ff + k;
+  const size_t gs = (size_t)ev.n_bins;
   // products C_j g_j as q_j + e_j (q_j = fl(Ch g.x); e_j its rounding error plus the Ch g.y and
   // Cl g.x cross terms), then an error-free pairwise sum of the q_j (depth 3 instead of a chain
   // of 8) whose errors join the low part
@@ -571,7 +573,7 @@ __device__ __forceinline__ void bin_accumulate_ff(const EventDev& ev, const Walk
   float sl = p.ph0l;
 #pragma unroll
   for (int j = 0; j < kBasis; ++j) {
-    const float2 gj = g[j];
+    const float2 gj = g[j * gs];
     q[j] = p.Ch[j] * gj.x;
     float e = fmaf(p.Ch[j], gj.x, -q[j]);
     e = fmaf(p.Ch[j], gj.y, e);

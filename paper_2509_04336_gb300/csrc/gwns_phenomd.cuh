@@ -265,7 +265,7 @@ __device__ __forceinline__ void pd_accumulate_mixed(const EventDev& ev, const Wa
     extra = e.at_scalef * atanf((e.Mf * (float)f - e.at_cf) * e.at_invf);
   }
   const float ff = (float)f;
-  const float amp = pd_amp_f32(e, k, ff, ev.basis_ff[(size_t)k * kBasisPD + 4].x);
+  const float amp = pd_amp_f32(e, k, ff, ev.basis_ff[(size_t)4 * ev.n_bins + k].x);
 #pragma unroll
   for (int det = 0; det < NDET; ++det) {
     double ph = fma(p.tau[det], f, phi);
@@ -295,30 +295,31 @@ __device__ __forceinline__ void ff_term(float& sh, float& sl, float ch, float cl
 template <int NDET>
 __device__ __forceinline__ void pd_accumulate_ff(const EventDev& ev, const WalkerParams& p, const PhenomExtra& e, int k,
                                                  AccPD32& acc) {
-  const float2* g = ev.basis_ff + (size_t)k * kBasisPD;
-  const float ff = g[13].x;   // f (exact on the grids used: f_min + k df in FP32)
+  const float2* g = ev.basis_ff + k;
+  const size_t gs = (size_t)ev.n_bins;
+  const float ff = g[13 * gs].x;   // f (exact on the grids used: f_min + k df in FP32)
   float sh, sl, extra = 0.f;
   if (k < e.k1) {
     sh = p.ph0h; sl = p.ph0l;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) ff_term(sh, sl, p.Ch[j], p.Cl[j], g[j]);
-    ff_term(sh, sl, e.Cxh[0], e.Cxl[0], g[8]);
-    ff_term(sh, sl, e.Cxh[1], e.Cxl[1], g[9]);
-    ff_term(sh, sl, e.Cxh[2], e.Cxl[2], g[10]);
+    for (int j = 0; j < 8; ++j) ff_term(sh, sl, p.Ch[j], p.Cl[j], g[j * gs]);
+    ff_term(sh, sl, e.Cxh[0], e.Cxl[0], g[8 * gs]);
+    ff_term(sh, sl, e.Cxh[1], e.Cxl[1], g[9 * gs]);
+    ff_term(sh, sl, e.Cxh[2], e.Cxl[2], g[10 * gs]);
   } else if (k < e.k2) {
     sh = e.ph0_int_h; sl = e.ph0_int_l;
-    ff_term(sh, sl, e.Cxh[3], e.Cxl[3], g[6]);
-    ff_term(sh, sl, e.Cxh[4], e.Cxl[4], g[11]);
-    ff_term(sh, sl, e.Cxh[5], e.Cxl[5], g[13]);
+    ff_term(sh, sl, e.Cxh[3], e.Cxl[3], g[6 * gs]);
+    ff_term(sh, sl, e.Cxh[4], e.Cxl[4], g[11 * gs]);
+    ff_term(sh, sl, e.Cxh[5], e.Cxl[5], g[13 * gs]);
   } else {
     sh = e.ph0_mr_h; sl = e.ph0_mr_l;
-    ff_term(sh, sl, e.Cxh[6], e.Cxl[6], g[1]);
-    ff_term(sh, sl, e.Cxh[7], e.Cxl[7], g[12]);
-    ff_term(sh, sl, e.Cxh[8], e.Cxl[8], g[13]);
+    ff_term(sh, sl, e.Cxh[6], e.Cxl[6], g[1 * gs]);
+    ff_term(sh, sl, e.Cxh[7], e.Cxl[7], g[12 * gs]);
+    ff_term(sh, sl, e.Cxh[8], e.Cxl[8], g[13 * gs]);
     extra = e.at_scalef * atanf((e.Mf * ff - e.at_cf) * e.at_invf);
   }
   const float r0 = (sh - rintf(sh)) + sl + extra;
-  const float amp = pd_amp_f32(e, k, ff, g[4].x);
+  const float amp = pd_amp_f32(e, k, ff, g[4 * gs].x);
   const float kf = (float)k;
 #pragma unroll
   for (int det = 0; det < NDET; ++det) {

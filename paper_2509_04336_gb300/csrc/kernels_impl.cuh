@@ -26,6 +26,13 @@ __device__ unsigned int g_walk_sm_arrivals[256];
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxVals = 3 * kMaxDet;   // (re, im, hh) per detector
 
+// (x >> 12) + 1/2 as a float (relative error ~1e-7) from two 32-bit conversions: a 64-bit
+// integer conversion runs on the FP64 pipe.
+__device__ __forceinline__ float top52_half_f(uint64_t x) {
+  const uint64_t v = x >> 12;
+  return fmaf(__uint2float_rn((uint32_t)(v >> 20)), 1048576.0f, __uint2float_rn((uint32_t)(v & 0xFFFFFull)) + 0.5f);
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   float bb = s - a;
@@ -515,10 +522,9 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
       if ((A.v[2] >> 63) == 0ull) {
         Philox4 B = philox4x64((uint64_t)step, wid, it, 1ull, T.key0, T.key1);
         // log2 U_i = log2((x_i >> 12) + 1/2) - 52, each factor's integer rounded to float
-        // (relative error 6e-8, no truncation, no underflow of the product)
-        float l2 = __log2f(__ull2float_rn(B.v[0] >> 12) + 0.5f) + __log2f(__ull2float_rn(B.v[1] >> 12) + 0.5f) +
-                   __log2f(__ull2float_rn(B.v[2] >> 12) + 0.5f) + __log2f(__ull2float_rn(B.v[3] >> 12) + 0.5f) -
-                   208.0f;
+        // (relative error ~1e-7, no truncation, no underflow of the product)
+        float l2 = __log2f(top52_half_f(B.v[0])) + __log2f(top52_half_f(B.v[1])) + __log2f(top52_half_f(B.v[2])) +
+                   __log2f(top52_half_f(B.v[3])) - 208.0f;
         sc = de_scale32 * (-0.25f * 0.6931471805599453f * l2);
       }
       // |x32 - x64| stays below ~1e-7 (1 + |s|) plus the log2 error times |s|: a margin of
