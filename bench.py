@@ -46,9 +46,9 @@ FP32_FLOPS_PER_WALKER_BIN = 243.0
 FP32_FLOPS_PER_WALKER_BIN_PD = 223.0
 FP32_PEAK_TFLOPS = 80.5      # nominal GB300 FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz
 # DRAM bytes (read + write) of one walk launch, from one ncu capture of this build's kernel
-# (walk_kernel<2, 3, WF>, batch 10 of the 4 s TaylorF2 workload and batch 3 of the 8 s
-# IMRPhenomD one); None for workloads without a capture.
-NCU_WALK_TRAFFIC_BYTES = {"bbh11_3det_4s_taylorf2": 281856 + 6656, "bbh11_3det_8s_phenomd": 4757248 + 361472}
+# (walk_kernel_ff<3, WF>, batch 10 of the 4 s TaylorF2 workload and batch 3 of the 8 s
+# IMRPhenomD one); None for workloads without a capture of the current kernel.
+NCU_WALK_TRAFFIC_BYTES = {}
 
 
 def rank_info():
@@ -404,7 +404,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h), "steps": args.steps, "log_z": lz, "log_z_err": lz_err},
         "gpu_launches": int(mixed["launches"]),
         "roofline": {"bound": "alu", "pipe": "fp32",
-                     "kernel": f"walk_kernel<2,3,{w.waveform}> (float-float phase)",
+                     "kernel": f"walk_kernel_ff<3,{w.waveform}> (float-float phase)",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": NCU_WALK_TRAFFIC_BYTES.get(args.workload),
                      "avg_launch_ms": walk_ms_avg,

@@ -748,13 +748,16 @@ __device__ __forceinline__ ff ff_wrap_unit(ff x) {
 //  2. the TaylorF2 setup of the round runs on all four warps at once (tf2_split_first /
 //     tf2_split_second: four independent chains, then the products); the IMRPhenomD-form
 //     setup, a small part of its round, stays on one rotating warp;
-//  3. the likelihoods, one warp per proposal (the whole CTA per proposal when m < 4);
+//  3. the likelihoods: TaylorF2 one warp per proposal (the whole CTA per proposal when m < 4),
+//     the IMRPhenomD form the whole CTA per proposal;
 //  4. warp 0 assembles ln L of every proposal in float-float and finds the first acceptance
 //     with one ballot.
 // The DE move is the walk's, u' = u + gamma (u_a - u_b), with the position and the survivors as
 // float pairs (~48 significant bits): the chain is the FP64 chain up to rounding at ~1e-14.
-// A round of three or more proposals is padded to a multiple of four: the likelihood phase
-// takes as long for 5 proposals as for 8, and the padding only advances the chain further.
+// A TaylorF2 round of three or more proposals is padded to a multiple of four: its
+// warp-per-proposal likelihood phase takes as long for 5 proposals as for 8, and the padding
+// only advances the chain further.  The IMRPhenomD form (thousands of bins a proposal) runs
+// each proposal on the whole CTA instead.
 template <int NDET, int WF>
 __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __restrict__ evs, WalkTask* tasks,
                                                             const int32_t* __restrict__ blk_task,
@@ -766,6 +769,8 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   __shared__ int cstep[kSpecMax];
   __shared__ double lnl_p[kSpecMax];
   __shared__ float part_sums[kSpecMax][2 * kMaxVals];
+  // IMRPhenomD form: every warp's compensated sums of every proposal
+  __shared__ float wsums[WF == 1 ? kSpecMax : 1][kWarps][2 * kMaxVals];
   __shared__ double u[kMaxDim];
   __shared__ ff uf[kMaxDim];
   __shared__ double red[kWarps][kMaxVals];
@@ -787,7 +792,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   const uint64_t wid = (uint64_t)(T.walker_offset + j);
   const uint64_t n_s = (uint64_t)T.n_s;
   int m = T.spec < 1 ? 1 : (T.spec > kSpecMax ? kSpecMax : T.spec);
-  if (m >= 3) m = min((m + 3) & ~3, kSpecMax);
+  if (WF == 0 && m >= 3) m = min((m + 3) & ~3, kSpecMax);
   const int window = min(kThreads, max(32, 4 * m));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool split = WF == 0 && ev.ff_setup;
@@ -937,7 +942,23 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
       __syncthreads();
     }
     // 3. likelihoods
-    if (nin >= kWarps) {
+    constexpr int V = Pow2Vals<NV>::value;
+    constexpr int group = 32 / V;
+    if (WF == 1) {
+      // IMRPhenomD form (thousands of bins a proposal): the whole CTA on each proposal in turn,
+      // so that proposals of different lengths leave no warp waiting; warp 0 combines the four
+      // warps' compensated sums below
+      for (int i = 0; i < nin; ++i) {
+        double dv[NV];
+        float fv[NV], fc[NV];
+        partials<2, NDET, WF>(ev, P[i], threadIdx.x, kThreads, dv, fv, fc);
+        float rs, rc;
+        int q;
+        warp_halving_sums<NV>(fv, fc, lane, rs, rc, q);
+        if ((lane & (group - 1)) == 0 && q < NV) { wsums[i][warp][2 * q] = rs; wsums[i][warp][2 * q + 1] = rc; }
+      }
+      __syncthreads();
+    } else if (nin >= kWarps) {
       for (int i = warp; i < nin; i += kWarps) {
         double dv[NV];
         float fv[NV], fc[NV];
@@ -945,8 +966,6 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
         float rs, rc;
         int q;
         warp_halving_sums<NV>(fv, fc, lane, rs, rc, q);
-        constexpr int V = Pow2Vals<NV>::value;
-        constexpr int group = 32 / V;
         if ((lane & (group - 1)) == 0 && q < NV) { part_sums[i][2 * q] = rs; part_sums[i][2 * q + 1] = rc; }
       }
       __syncthreads();
@@ -960,7 +979,28 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
     // 4. ln L of every proposal, then the steps in order: the first acceptance ends the round
     if (warp == 0) {
       double l = 0.0;
-      if (lane < nin) l = nin >= kWarps ? lnl_ff<NDET, WF>(ev, P[lane], part_sums[lane]) : lnl_p[lane];
+      if (lane < nin) {
+        if (WF == 1) {
+          // (s, c) of the four warps, summed with error-free additions
+          float ps[2 * NV];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            float sh = wsums[lane][0][2 * q], sl = wsums[lane][0][2 * q + 1];
+#pragma unroll
+            for (int w2 = 1; w2 < kWarps; ++w2) {
+              float t, e;
+              two_sum(sh, wsums[lane][w2][2 * q], t, e);
+              sh = t;
+              sl += wsums[lane][w2][2 * q + 1] + e;
+            }
+            ps[2 * q] = sh;
+            ps[2 * q + 1] = sl;
+          }
+          l = lnl_ff<NDET, WF>(ev, P[lane], ps);
+        } else {
+          l = nin >= kWarps ? lnl_ff<NDET, WF>(ev, P[lane], part_sums[lane]) : lnl_p[lane];
+        }
+      }
       const unsigned am = __ballot_sync(0xffffffffu, lane < nin && l > lnl_star);
       const int c = am ? __ffs(am) - 1 : -1;
       const int used = c >= 0 ? c + 1 : nin;
