@@ -23,6 +23,7 @@ struct Scratch {
 // it in place, so a captured graph replays batches without host round trips.
 struct NsState {
   double log_x, log_z, lnl_star, dlogz, mean_accept, lnl_max, delay_k, term_value;
+  double spec_mult, spec_p;   // speculation rule m = spec_mult / p; p of the last batch
   int64_t n_dead, n_like, iteration, max_iter, dead_cap, n_bins_eval, n_spec_eval;
   int32_t n_live, k, D, n_steps, naccept, maxmcmc, term_kind, done, zero_accept, overflow;
   int32_t spec, spec_auto, spec_cap, spec_rule;   // spec = min(spec_rule, spec_cap)
@@ -85,11 +86,12 @@ struct ns_handle {
   double walk_ms = 0.0;
   int64_t kernel_launches = 0;
   int64_t launches_per_batch[9] = {};   // kernels in each cached graph, per batch count
-  // speculation-depth autotuner (all events in automatic mode)
+  // speculation-depth autotuner (all events in automatic mode): picks the cap
   bool tune = false;
-  int tune_next = 3;                 // iteration at which the next tuning pass starts
-  int tune_idx = -1;                 // candidate under trial, -1 when not tuning
-  double tune_cost[8] = {0};
+  bool tune_guessed = false;         // first cap set from the cost structure (after batch 1)
+  int tune_next = 64;                // iteration at which the next tuning pass starts
+  int tune_idx = -1;                 // step of the tuning pass, -1 when not tuning
+  double tune_ms[8] = {0}, tune_calls[8] = {0};   // per candidate, summed over its trials
   int tune_best = 32;
   std::vector<gwns::NsState> host_ns;   // last progress snapshot
   std::string err;

@@ -234,12 +234,14 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
     S.n_like += (int64_t)tot_calls;
     S.n_bins_eval += (int64_t)tot_bins;
     S.n_spec_eval += (int64_t)tot_spec;
-    // speculation depth of the next batch: about 0.7 / p in-bounds proposals per round,
-    // p the acceptance per likelihood call of this batch, so that the first acceptance
-    // falls on average about halfway through a round
+    // speculation depth of the next batch: about c / p in-bounds proposals per round, p the
+    // acceptance per likelihood call of this batch; c = 1.4 puts the first acceptance on
+    // average in the first two thirds of a round (c = 0.7: halfway), a trade of discarded
+    // proposals for fewer rounds, whose fixed costs dominate short likelihoods
     if (S.spec_auto) {
       double p = mean_acc / fmax(tot_calls / (double)k, 1.0);
-      double m = p > 0.0 ? floor(0.7 / p + 0.5) : (double)kSpecMax;
+      S.spec_p = p;
+      double m = p > 0.0 ? floor(S.spec_mult / p + 0.5) : (double)kSpecMax;
       S.spec_rule = (int32_t)fmin(fmax(m, 1.0), (double)kSpecMax);
       S.spec = min(S.spec_rule, S.spec_cap);
     }
@@ -484,6 +486,8 @@ int nested_init(ns_handle* h) {
     S.spec_cap = h->precision == 0 ? 8 : kSpecMax;
     S.spec_rule = 4;
     S.spec = c.spec_depth > 0 ? c.spec_depth : 4;
+    S.spec_mult = 1.4;
+    S.spec_p = 0.0;
     const size_t n = S.n_live, k = S.k, D = S.D;
     if ((r = alloc(h, (void**)&S.live_u, sizeof(double) * n * D, "live_u")) ||
         (r = alloc(h, (void**)&S.live_lnl, sizeof(double) * n, "live_lnl")) ||
@@ -583,16 +587,19 @@ static void fill_progress(ns_handle* h, ns_progress* p) {
 }
 
 namespace {
-// Candidate caps of the speculation depth tried by the autotuner.
+// Candidate caps of the speculation depth tried by the autotuner (the rule m = c / p sets the
+// depth below the cap): a small cap suits proposals with much work of their own, where each
+// speculative one costs a full evaluation; short likelihoods, whose rounds are dominated by
+// their fixed costs, take the largest.
 const int kTuneCaps[] = {2, 4, 8, 16, 32};
 const int kTuneCapsF64[] = {1, 2, 4, 8};
 
-// Sets the speculation cap of every event, and the depth of the next walk to the rule
-// value under that cap.
+// Sets the speculation cap of every event, and the depth of the next walk to the rule value
+// under that cap.
 int set_spec_cap(ns_handle* h, int cap) {
   for (size_t e = 0; e < h->events.size(); ++e) {
     const NsState& S = h->host_ns[e];
-    int32_t spec = S.spec_rule < cap ? S.spec_rule : cap;
+    const int32_t spec = S.spec_rule < cap ? S.spec_rule : cap;
     NsState* d = h->d_ns + e;
     cudaError_t err;
     if ((err = cudaMemcpy(&d->spec_cap, &cap, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
@@ -621,16 +628,36 @@ extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
   const int n_caps = h->precision == 0 ? 4 : 5;
   while (left > 0) {
     int b = left < G ? left : G;
-    // Autotuning of the speculation cap: from iteration tune_next, one batch per candidate,
-    // scored by walk-kernel device time per likelihood call; the best cap is kept until the
-    // next pass 32 iterations later.  Any depth gives the same chain, so this only moves time.
+    // Autotuning of the speculation cap: from iteration tune_next, one batch per candidate
+    // in the order c_0 .. c_{n-1}, c_{n-1} .. c_0 (the sampler's regime drifts from
+    // batch to batch; the mirrored order cancels a linear drift), scored by summed walk-kernel
+    // device time per likelihood call; the best is kept until the next pass 64 iterations
+    // later.  Any depth gives the chain of the one-step walk (exactly in FP64), so this only
+    // moves time.
     int64_t it_now = h->host_ns.empty() ? 0 : h->host_ns[0].iteration;
+    // First cap, from the cost structure once a batch has run: a proposal of fewer than ~1k
+    // active bins is a short likelihood whose rounds are dominated by fixed costs (largest
+    // cap); a longer one costs a full evaluation per speculative proposal (small cap).
+    if (h->tune && !h->tune_guessed && it_now >= 1) {
+      double bins = 0.0, evals = 0.0;
+      for (auto& S : h->host_ns) { bins += (double)S.n_bins_eval; evals += (double)S.n_spec_eval; }
+      const bool short_lik = evals > 0.0 && bins < 1024.0 * evals;
+      const int cap = h->precision == 0 ? (short_lik ? 8 : 2) : (short_lik ? 32 : 4);
+      if ((r = set_spec_cap(h, cap))) return r;
+      h->tune_best = cap;
+      h->tune_guessed = true;
+    }
     int64_t like0 = 0;
     double ms0 = h->walk_ms;
     bool trial = false;
+    int cand = 0;
     if (h->tune && (h->tune_idx >= 0 || it_now >= h->tune_next)) {
-      if (h->tune_idx < 0) h->tune_idx = 0;
-      if ((r = set_spec_cap(h, caps[h->tune_idx]))) return r;
+      if (h->tune_idx < 0) {
+        h->tune_idx = 0;
+        for (int i = 0; i < n_caps; ++i) h->tune_ms[i] = h->tune_calls[i] = 0.0;
+      }
+      cand = h->tune_idx < n_caps ? h->tune_idx : 2 * n_caps - 1 - h->tune_idx;
+      if ((r = set_spec_cap(h, caps[cand]))) return r;
       for (auto& S : h->host_ns) like0 += S.n_like;
       b = 1;
       trial = true;
@@ -650,14 +677,19 @@ extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
     if (trial) {
       int64_t like1 = 0;
       for (auto& S : h->host_ns) like1 += S.n_like;
-      h->tune_cost[h->tune_idx] = (h->walk_ms - ms0) / (double)(like1 > like0 ? like1 - like0 : 1);
-      if (++h->tune_idx == n_caps) {
+      h->tune_ms[cand] += h->walk_ms - ms0;
+      h->tune_calls[cand] += (double)(like1 - like0);
+      if (++h->tune_idx == 2 * n_caps) {
         int best = 0;
-        for (int i = 1; i < n_caps; ++i) if (h->tune_cost[i] < h->tune_cost[best]) best = i;
+        double best_cost = INFINITY;
+        for (int i = 0; i < n_caps; ++i) {
+          const double cost = h->tune_ms[i] / (h->tune_calls[i] > 0.0 ? h->tune_calls[i] : 1.0);
+          if (cost < best_cost) { best_cost = cost; best = i; }
+        }
         h->tune_best = caps[best];
         if ((r = set_spec_cap(h, h->tune_best))) return r;
         h->tune_idx = -1;
-        h->tune_next = (int)h->host_ns[0].iteration + 32;
+        h->tune_next = (int)h->host_ns[0].iteration + 64;
       }
     }
     left -= b;
@@ -762,7 +794,7 @@ extern "C" int ns_posterior(ns_handle* h, int event, double* theta_out, double* 
 
 // ---------------------------------------------------------------- checkpoint / resume
 namespace {
-const char kMagic[8] = {'G', 'W', 'N', 'S', 'S', 'T', '0', '2'};
+const char kMagic[8] = {'G', 'W', 'N', 'S', 'S', 'T', '0', '3'};
 
 bool wr(FILE* f, const void* p, size_t n) { return fwrite(p, 1, n, f) == n; }
 bool rd(FILE* f, void* p, size_t n) { return fread(p, 1, n, f) == n; }
