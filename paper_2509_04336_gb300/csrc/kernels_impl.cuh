@@ -420,6 +420,7 @@ __global__ void __launch_bounds__(256) waveform_kernel(const EventDev* __restric
 }
 
 // ---------------------------------------------------------------- acceptance walk
+// Modes 0 and 1 (FP64 phase); mode 2 runs walk_kernel_ff below.
 // One CTA per walker, persistent over the walk.  A round looks ahead over the next W steps:
 //  1. the DE draws of a step depend only on its Philox counter (step, walker, iteration,
 //     tag), not on the chain, so every thread screens one candidate step in FP32 from the
@@ -596,15 +597,9 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
           sc = 1.0;
         } else {
           Philox4 B = philox4x64((uint64_t)st, wid, it, 1ull, T.key0, T.key1);
-          if (PREC == 2) {   // float-float logarithm: the FP64 pipe is left to the likelihoods
-            const ff lp = ff_log_uniform_product(B.v);
-            const ff scf = ff_mul(ff_mul_f(lp, -0.25f), ff_from_double(de_scale));
-            sc = (double)scf.h + (double)scf.l;
-          } else {
-            double prod = __dmul_rn(__dmul_rn(__dmul_rn(rand_open_unit(B.v[0]), rand_open_unit(B.v[1])),
-                                              rand_open_unit(B.v[2])), rand_open_unit(B.v[3]));
-            sc = __dmul_rn(de_scale, __dmul_rn(-0.25, log(prod)));
-          }
+          double prod = __dmul_rn(__dmul_rn(__dmul_rn(rand_open_unit(B.v[0]), rand_open_unit(B.v[1])),
+                                            rand_open_unit(B.v[2])), rand_open_unit(B.v[3]));
+          sc = __dmul_rn(de_scale, __dmul_rn(-0.25, log(prod)));
         }
         const double* ua = T.surv + a * D;
         const double* ub = T.surv + b * D;
@@ -669,14 +664,10 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
       if (PREC != 0) {
         __syncthreads();
         if (warp == sw && lane < nin) {
-          if (PREC == 2) {
-            lnl_p[lane] = lnl_ff<NDET, WF>(ev, P[lane], part_sums[lane]);
-          } else {
-            double v[NV];
+          double v[NV];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) v[q] = (double)part_sums[lane][2 * q] + (double)part_sums[lane][2 * q + 1];
-            lnl_p[lane] = lnl_from_vals<PREC, NDET, WF>(ev, P[lane], v);
-          }
+          for (int q = 0; q < NV; ++q) v[q] = (double)part_sums[lane][2 * q] + (double)part_sums[lane][2 * q + 1];
+          lnl_p[lane] = lnl_from_vals<PREC, NDET, WF>(ev, P[lane], v);
         }
       }
     } else {
@@ -748,16 +739,16 @@ __device__ __forceinline__ ff ff_wrap_unit(ff x) {
 //  2. the TaylorF2 setup of the round runs on all four warps at once (tf2_split_first /
 //     tf2_split_second: four independent chains, then the products); the IMRPhenomD-form
 //     setup, a small part of its round, stays on one rotating warp;
-//  3. the likelihoods: TaylorF2 one warp per proposal (the whole CTA per proposal when m < 4),
-//     the IMRPhenomD form the whole CTA per proposal;
+//  3. the likelihoods: TaylorF2 one warp per proposal, the IMRPhenomD form the whole CTA per
+//     proposal;
 //  4. warp 0 assembles ln L of every proposal in float-float and finds the first acceptance
 //     with one ballot.
 // The DE move is the walk's, u' = u + gamma (u_a - u_b), with the position and the survivors as
 // float pairs (~48 significant bits): the chain is the FP64 chain up to rounding at ~1e-14.
-// A TaylorF2 round of three or more proposals is padded to a multiple of four: its
-// warp-per-proposal likelihood phase takes as long for 5 proposals as for 8, and the padding
-// only advances the chain further.  The IMRPhenomD form (thousands of bins a proposal) runs
-// each proposal on the whole CTA instead.
+// A TaylorF2 round is padded to a multiple of four proposals: its warp-per-proposal likelihood
+// phase takes as long for 1 or 5 proposals as for 4 or 8, and the padding only advances the
+// chain further.  The IMRPhenomD form (thousands of bins a proposal) runs each proposal on the
+// whole CTA instead.
 template <int NDET, int WF>
 __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __restrict__ evs, WalkTask* tasks,
                                                             const int32_t* __restrict__ blk_task,
@@ -767,14 +758,11 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   __shared__ ff propf[kSpecMax][kMaxDim];
   __shared__ TF2Part parts[WF == 0 ? kSpecMax : 1];
   __shared__ int cstep[kSpecMax];
-  __shared__ double lnl_p[kSpecMax];
   __shared__ float part_sums[kSpecMax][2 * kMaxVals];
   // IMRPhenomD form: every warp's compensated sums of every proposal
   __shared__ float wsums[WF == 1 ? kSpecMax : 1][kWarps][2 * kMaxVals];
   __shared__ double u[kMaxDim];
   __shared__ ff uf[kMaxDim];
-  __shared__ double red[kWarps][kMaxVals];
-  __shared__ double vals[kMaxVals];
   __shared__ int wcount[kWarps];
   __shared__ int s_next, s_setup_warp, s_end, s_needq;
   __shared__ int s_isflow[kSpecMax];
@@ -792,7 +780,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   const uint64_t wid = (uint64_t)(T.walker_offset + j);
   const uint64_t n_s = (uint64_t)T.n_s;
   int m = T.spec < 1 ? 1 : (T.spec > kSpecMax ? kSpecMax : T.spec);
-  if (WF == 0 && m >= 3) m = min((m + 3) & ~3, kSpecMax);
+  if (WF == 0) m = min((m + 3) & ~3, kSpecMax);
   const int window = min(kThreads, max(32, 4 * m));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool split = WF == 0 && ev.ff_setup;
@@ -958,7 +946,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
         if ((lane & (group - 1)) == 0 && q < NV) { wsums[i][warp][2 * q] = rs; wsums[i][warp][2 * q + 1] = rc; }
       }
       __syncthreads();
-    } else if (nin >= kWarps) {
+    } else {
       for (int i = warp; i < nin; i += kWarps) {
         double dv[NV];
         float fv[NV], fc[NV];
@@ -969,12 +957,6 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
         if ((lane & (group - 1)) == 0 && q < NV) { part_sums[i][2 * q] = rs; part_sums[i][2 * q + 1] = rc; }
       }
       __syncthreads();
-    } else {
-      for (int i = 0; i < nin; ++i) {
-        cta_sums<2, NDET, WF>(ev, P[i], red, vals);
-        if (threadIdx.x == 0) lnl_p[i] = lnl_from_vals<2, NDET, WF>(ev, P[i], vals);
-        __syncthreads();
-      }
     }
     // 4. ln L of every proposal, then the steps in order: the first acceptance ends the round
     if (warp == 0) {
@@ -998,7 +980,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
           }
           l = lnl_ff<NDET, WF>(ev, P[lane], ps);
         } else {
-          l = nin >= kWarps ? lnl_ff<NDET, WF>(ev, P[lane], part_sums[lane]) : lnl_p[lane];
+          l = lnl_ff<NDET, WF>(ev, P[lane], part_sums[lane]);
         }
       }
       const unsigned am = __ballot_sync(0xffffffffu, lane < nin && l > lnl_star);

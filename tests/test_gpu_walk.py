@@ -45,8 +45,11 @@ def walk_inputs(w, ev, n_surv, n_walk, seed):
     ("bbh11_3det_4s_taylorf2", synth.PREC_FP64, 8),
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED, 32),
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, 2),
+    ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, 3),    # padded to 4: one proposal per warp
+    ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, 5),    # padded to 8
     ("bbh11_3det_4s_taylorf2", synth.PREC_MIXED_FF, 32),
     ("bbh11_3det_8s_phenomd", synth.PREC_FP64, 8),
+    ("bbh11_3det_8s_phenomd", synth.PREC_MIXED_FF, 1),
     ("bbh11_3det_8s_phenomd", synth.PREC_MIXED_FF, 2),
     ("bbh11_3det_8s_phenomd", synth.PREC_MIXED_FF, 16),
 ])
