@@ -20,7 +20,8 @@ struct Scratch {
 };
 
 // Device-resident nested-sampling state of one event.  The batch kernels read and write
-// it in place, so a captured graph replays batches without host round trips.
+// it in place, so a captured graph replays batches without host round trips.  The buffer
+// pointers come last, from live_u on: a checkpoint restores the fields before them.
 struct NsState {
   double log_x, log_z, lnl_star, dlogz, mean_accept, lnl_max, delay_k, term_value;
   double spec_mult, spec_p;   // speculation rule m = spec_mult / p; p of the last batch
@@ -112,4 +113,11 @@ int flow_enqueue_train(ns_handle* h, int e, cudaStream_t s, int64_t* launches);
 int flow_enqueue_table(ns_handle* h, int e, cudaStream_t s, int64_t* launches);
 int flow_attach(ns_handle* h, int event, gwns::WalkTask& T, int n, int n_steps, gwns::Scratch* table, cudaStream_t s);
 bool flow_state_write(ns_handle* h, int e, FILE* f);
-bool flow_state_read(ns_handle* h, int e, FILE* f);
+// A checkpoint's flow record, read and checked against the handle before anything is applied.
+struct FlowBlob {
+  bool present = false;
+  gwns::FlowDev F;
+  std::vector<float> buf;   // master weights, Adam m, Adam v
+};
+bool flow_state_parse(ns_handle* h, int e, FILE* f, FlowBlob& b);
+bool flow_state_apply(ns_handle* h, int e, const FlowBlob& b);

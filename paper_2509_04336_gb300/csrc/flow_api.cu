@@ -230,23 +230,31 @@ bool flow_state_write(ns_handle* h, int e, FILE* f) {
   return fwrite(&F, sizeof(F), 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
 }
 
-bool flow_state_read(ns_handle* h, int e, FILE* f) {
+bool flow_state_parse(ns_handle* h, int e, FILE* f, FlowBlob& b) {
+  const EventHost& E = h->events[e];
+  const FlowHost& Fh = E.flow;
+  b.present = Fh.enabled;
+  if (!Fh.enabled) return true;
+  b.buf.assign((size_t)Fh.n_params * 3, 0.0f);
+  if (fread(&b.F, sizeof(b.F), 1, f) != 1 || fread(b.buf.data(), sizeof(float), b.buf.size(), f) != b.buf.size())
+    return false;
+  return b.F.n_params == Fh.n_params && b.F.n_layers == Fh.n_layers && b.F.n_dim == E.n_dim;
+}
+
+bool flow_state_apply(ns_handle* h, int e, const FlowBlob& b) {
+  if (!b.present) return true;
   EventHost& E = h->events[e];
   FlowHost& Fh = E.flow;
-  if (!Fh.enabled) return true;
-  FlowDev F;
-  std::vector<float> buf((size_t)Fh.n_params * 3);
-  if (fread(&F, sizeof(F), 1, f) != 1 || fread(buf.data(), sizeof(float), buf.size(), f) != buf.size()) return false;
-  if (F.n_params != Fh.n_params || F.n_layers != Fh.n_layers || F.n_dim != E.n_dim) return false;
   FlowDev cur = host_flowdev(E);
-  std::memcpy(cur.mu, F.mu, sizeof(F.mu));
-  std::memcpy(cur.sigma, F.sigma, sizeof(F.sigma));
-  cur.log_sigma_sum = F.log_sigma_sum;
-  cur.adam_t = F.adam_t;
+  std::memcpy(cur.mu, b.F.mu, sizeof(b.F.mu));
+  std::memcpy(cur.sigma, b.F.sigma, sizeof(b.F.sigma));
+  cur.log_sigma_sum = b.F.log_sigma_sum;
+  cur.adam_t = b.F.adam_t;
+  const float* buf = b.buf.data();
   return cudaMemcpy(Fh.d_flow, &cur, sizeof(cur), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(Fh.d_master, buf.data(), sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(Fh.d_m, buf.data() + Fh.n_params, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(Fh.d_v, buf.data() + 2 * (size_t)Fh.n_params, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) ==
+         cudaMemcpy(Fh.d_master, buf, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(Fh.d_m, buf + Fh.n_params, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(Fh.d_v, buf + 2 * (size_t)Fh.n_params, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) ==
              cudaSuccess &&
          launch_flow_pack(Fh.d_flow, Fh.d_img, Fh.d_bias, Fh.d_master, Fh.n_params, h->stream) == cudaSuccess &&
          cudaStreamSynchronize(h->stream) == cudaSuccess;

@@ -320,6 +320,7 @@ __device__ __forceinline__ void pd_accumulate_ff(const EventDev& ev, const Walke
   }
   const float r0 = (sh - rintf(sh)) + sl + extra;
   const float amp = pd_amp_f32(e, k, ff, g[4 * gs].x);
+  const float amp2 = amp * amp;
   const float kf = (float)k;
 #pragma unroll
   for (int det = 0; det < NDET; ++det) {
@@ -332,7 +333,9 @@ __device__ __forceinline__ void pd_accumulate_ff(const EventDev& ev, const Walke
     float2 z = ev.z32[(size_t)det * ev.n_bins + k];
     kahan_add(acc.re[det], acc.cre[det], amp * fmaf(z.x, c, z.y * s));
     kahan_add(acc.im[det], acc.cim[det], amp * fmaf(z.y, c, -z.x * s));
-    kahan_add(acc.hh[det], acc.chh[det], amp * amp * ev.gw32[(size_t)det * ev.n_bins + k]);
+    // template power: positive terms, no cancellation -- a plain FP32 sum per lane (the lanes'
+    // sums are combined with error-free additions)
+    acc.hh[det] = fmaf(amp2, ev.gw32[(size_t)det * ev.n_bins + k], acc.hh[det]);
   }
 }
 

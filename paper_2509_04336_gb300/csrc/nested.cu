@@ -14,6 +14,7 @@
 //           retuned from the batch mean accepted count, and the termination test runs.
 // ns_step replays a CUDA graph of G batches and reads the small NsState back once per replay.
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -840,39 +841,61 @@ extern "C" int ns_state_load(ns_handle* h, const char* path) {
   cudaSetDevice(h->device);
   FILE* f = fopen(path, "rb");
   if (!f) return set_error(h, NS_EIO, "cannot open %s", path);
+  // 1. read and check the whole file on the host; the handle is untouched until it all fits
+  struct Rec {
+    NsState S;
+    std::vector<double> live_u, live_lnl, dead_u, dead_lnl, dead_logw;
+    std::vector<int32_t> dead_nlive;
+    FlowBlob flow;
+  };
   char magic[8];
   int32_t ne = 0;
   bool ok = rd(f, magic, 8) && std::memcmp(magic, kMagic, 8) == 0 && rd(f, &ne, sizeof(ne)) &&
             ne == (int32_t)h->events.size();
-  std::vector<NsState> saved(ok ? ne : 0);
+  std::vector<Rec> recs(ok ? ne : 0);
+  auto rdv = [&](auto& v, size_t n) {
+    v.resize(n);
+    return rd(f, v.data(), sizeof(v[0]) * n);
+  };
   for (int e = 0; e < ne && ok; ++e) {
-    NsState& S = saved[e];
-    ok = rd(f, &S, sizeof(S));
-    EventHost& E = h->events[e];
-    ok = ok && S.n_live == E.ns.n_live && S.k == E.ns.k && S.D == E.ns.D;
+    Rec& R = recs[e];
+    const NsState& cur = h->events[e].ns;
+    ok = rd(f, &R.S, sizeof(R.S)) && R.S.n_live == cur.n_live && R.S.k == cur.k && R.S.D == cur.D &&
+         R.S.n_dead >= 0 && R.S.n_dead <= (int64_t)1 << 40;
     if (!ok) break;
-    if (grow_dead(h, e, S.n_dead, 0)) { ok = false; break; }
-    ok = ok && dev_read(f, E.ns.live_u, (size_t)S.n_live * S.D) && dev_read(f, E.ns.live_lnl, (size_t)S.n_live);
-    ok = ok && dev_read(f, E.ns.dead_u, (size_t)S.n_dead * S.D) && dev_read(f, E.ns.dead_lnl, (size_t)S.n_dead);
-    ok = ok && dev_read(f, E.ns.dead_logw, (size_t)S.n_dead) && dev_read(f, E.ns.dead_nlive, (size_t)S.n_dead);
-    ok = ok && flow_state_read(h, e, f);
+    const size_t nl = (size_t)R.S.n_live, nd = (size_t)R.S.n_dead, D = (size_t)R.S.D;
+    ok = rdv(R.live_u, nl * D) && rdv(R.live_lnl, nl) && rdv(R.dead_u, nd * D) && rdv(R.dead_lnl, nd) &&
+         rdv(R.dead_logw, nd) && rdv(R.dead_nlive, nd) && flow_state_parse(h, e, f, R.flow);
   }
   fclose(f);
   if (!ok) return set_error(h, NS_EIO, "reading %s failed or it does not match this handle", path);
-  // restore the scalar state; keep this handle's own buffer pointers and capacity
+  // 2. apply
   for (int e = 0; e < ne; ++e) {
-    NsState S = saved[e];
-    const NsState& cur = h->events[e].ns;
-    S.live_u = cur.live_u; S.live_lnl = cur.live_lnl; S.surv_u = cur.surv_u; S.survf = cur.survf;
-    S.w_u0 = cur.w_u0; S.w_lnl0 = cur.w_lnl0; S.w_uo = cur.w_uo; S.w_lo = cur.w_lo;
-    S.w_na = cur.w_na; S.w_nl = cur.w_nl; S.slot = cur.slot;
-    S.dead_u = cur.dead_u; S.dead_lnl = cur.dead_lnl; S.dead_logw = cur.dead_logw; S.dead_nlive = cur.dead_nlive;
-    S.dead_cap = cur.dead_cap;
-    cudaMemcpy(h->d_ns + e, &S, sizeof(S), cudaMemcpyHostToDevice);
+    Rec& R = recs[e];
+    int r = grow_dead(h, e, R.S.n_dead, 0);
+    if (r) return r;
+    EventHost& E = h->events[e];
+    const size_t nl = (size_t)R.S.n_live, nd = (size_t)R.S.n_dead, D = (size_t)R.S.D;
+    cudaError_t err;
+    if ((err = cudaMemcpy(E.ns.live_u, R.live_u.data(), sizeof(double) * nl * D, cudaMemcpyHostToDevice)) ||
+        (err = cudaMemcpy(E.ns.live_lnl, R.live_lnl.data(), sizeof(double) * nl, cudaMemcpyHostToDevice)) ||
+        (nd && (err = cudaMemcpy(E.ns.dead_u, R.dead_u.data(), sizeof(double) * nd * D, cudaMemcpyHostToDevice))) ||
+        (nd && (err = cudaMemcpy(E.ns.dead_lnl, R.dead_lnl.data(), sizeof(double) * nd, cudaMemcpyHostToDevice))) ||
+        (nd && (err = cudaMemcpy(E.ns.dead_logw, R.dead_logw.data(), sizeof(double) * nd, cudaMemcpyHostToDevice))) ||
+        (nd && (err = cudaMemcpy(E.ns.dead_nlive, R.dead_nlive.data(), sizeof(int32_t) * nd, cudaMemcpyHostToDevice))))
+      return cuda_fail(h, err, "state upload");
+    if (!flow_state_apply(h, e, R.flow)) return set_error(h, NS_ECUDA, "flow state upload failed");
+    // the checkpoint's scalar state (every field before the buffer pointers); this handle keeps
+    // its own buffers and dead-store capacity
+    NsState S = E.ns;
+    std::memcpy(&S, &R.S, offsetof(NsState, live_u));
+    S.dead_cap = E.ns.dead_cap;
     WalkTask* dt = h->d_tasks + e;
-    cudaMemcpy(&dt->done, &S.done, sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(&dt->n_steps, &S.n_steps, sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(&dt->spec, &S.spec, sizeof(int32_t), cudaMemcpyHostToDevice);
+    if ((err = cudaMemcpy(h->d_ns + e, &S, sizeof(S), cudaMemcpyHostToDevice)) ||
+        (err = cudaMemcpy(&dt->done, &S.done, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+        (err = cudaMemcpy(&dt->n_steps, &S.n_steps, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+        (err = cudaMemcpy(&dt->spec, &S.spec, sizeof(int32_t), cudaMemcpyHostToDevice)))
+      return cuda_fail(h, err, "state upload");
   }
   return download_states(h);
 }

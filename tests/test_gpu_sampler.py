@@ -144,6 +144,37 @@ def test_resume_replays_the_uninterrupted_run(tmp_path, flow):
             assert np.array_equal(x, y)
 
 
+def test_truncated_state_leaves_the_handle_untouched(tmp_path):
+    # A checkpoint is read and checked in full before anything is applied.
+    w, ev, pri, ll = tiny()
+    path = os.path.join(tmp_path, "state.bin")
+    cut = os.path.join(tmp_path, "cut.bin")
+    cfg = lambda: gwns.make_config(w, pri, precision=synth.PREC_FP64, max_iter=6)
+    h = gwns.ns_init([cfg()], [ev])
+    try:
+        gwns.ns_step(h, 3)
+        gwns.ns_state_save(h, path)
+    finally:
+        gwns.ns_free(h)
+    with open(path, "rb") as fh:
+        blob = fh.read()
+    with open(cut, "wb") as fh:
+        fh.write(blob[: len(blob) - 100])
+    h = gwns.ns_init([cfg()], [ev])
+    try:
+        _, before = gwns.ns_step(h, 1)
+        th0, lw0 = gwns.ns_posterior(h, 0)
+        with pytest.raises(gwns.GwnsError) as e:
+            gwns.ns_state_load(h, cut)
+        assert e.value.code == gwns.NS_EIO
+        th1, lw1 = gwns.ns_posterior(h, 0)
+        assert np.array_equal(th0, th1) and np.array_equal(lw0, lw1)
+        _, after = gwns.ns_step(h, 1)
+        assert after[0]["iterations"] == before[0]["iterations"] + 1
+    finally:
+        gwns.ns_free(h)
+
+
 def test_state_load_rejects_a_mismatched_handle(tmp_path):
     w, ev, pri, ll = tiny()
     path = os.path.join(tmp_path, "state.bin")
