@@ -117,3 +117,46 @@ def test_likelihood_ragged_bins_small_event():
             assert np.all(np.abs(got - want) <= tol * np.maximum(np.abs(want), 1.0))
         finally:
             gwns.ns_free(h)
+
+
+def test_largest_batched_event_full_size():
+    # The 64-event population's 16 s events have 32,449 bins (20-2048 Hz at 1/16 Hz), the
+    # largest event the sampler is run on: ln L of sampled points against the oracle in the
+    # FP64 and float-float modes at full size, and a short float-float walk.
+    from oracle import prior as P, walk
+    w = synth.batched_workloads(8, seed=100)[2]
+    assert w.n_bins == 32449 and w.waveform == synth.PHENOMD_FORM
+    ev = synth.make_event(w, lambda e, d, th: L.project(e, d, th, w.waveform), L.inner)
+    pri = synth.priors_with_injection(w, ev)
+    u = synth.uniform_unit_cube(12, w.n_dim, 31)
+    th = np.ascontiguousarray(np.vstack([ev.theta_inj] + [P.transform(x, pri) for x in u]))
+    want = np.array([L.log_likelihood(ev, t, w.waveform, w.use_ratio) for t in th])
+    for prec, tol in ((synth.PREC_FP64, TOL_FP64), (synth.PREC_MIXED_FF, TOL_MIXED)):
+        h = gwns.ns_init([gwns.make_config(w, pri, precision=prec)], [ev])
+        try:
+            got = np.zeros(th.shape[0])
+            gwns.ns_likelihood_batch(h, 0, th, got)
+            scale = np.maximum(np.abs(want), 0.5 * w.snr ** 2)
+            assert np.all(np.abs(got - want) <= tol * scale), (prec, np.max(np.abs(got - want) / scale))
+        finally:
+            gwns.ns_free(h)
+    # walk: 6 walkers, 8 steps, from survivors above the 40 % quantile of 40 prior points
+    ll = lambda x: L.log_likelihood(ev, P.transform(x, pri), w.waveform, w.use_ratio)
+    surv = synth.uniform_unit_cube(40, w.n_dim, 32)
+    ls = np.array([ll(x) for x in surv])
+    star = float(np.quantile(ls, 0.4))
+    idx = np.where(ls > star)[0][:6]
+    u0, l0 = np.ascontiguousarray(surv[idx]), np.ascontiguousarray(ls[idx])
+    ou, ol, oa, on, margin = walk.acceptance_walk(ll, u0, l0, star, surv, 8, P.periodic_mask(pri), (w.seed, 0), 1)
+    h = gwns.ns_init([gwns.make_config(w, pri, precision=synth.PREC_MIXED_FF, spec_depth=4)], [ev])
+    try:
+        gu, gl = np.zeros_like(u0), np.zeros(6)
+        ga, gn = np.zeros(6, np.int32), np.zeros(6, np.int32)
+        gwns.ns_walk_batch(h, 0, np.ascontiguousarray(surv), u0, l0, star, 8, 1, 0, gu, gl, ga, gn)
+    finally:
+        gwns.ns_free(h)
+    same = margin > 4e-6 * max(abs(star), 1.0)
+    assert same.sum() >= 4
+    assert np.array_equal(ga[same], oa[same]) and np.array_equal(gn[same], on[same])
+    assert np.allclose(gu[same], ou[same], rtol=0, atol=1e-12)
+    assert np.all(gl > star)
