@@ -240,7 +240,7 @@ int ns_state_save(ns_handle* h, const char* path);
 int ns_state_load(ns_handle* h, const char* path);
 
 /* ---------------------------------------------------------------- Flow proposal
- * The paper (Sec. 6) motivates normalising-flow proposals for a batched GPU nested sampler
+ * The paper (Sec. 5) motivates normalising-flow proposals for a batched GPU nested sampler
  * without fixing a design; this library's reading (an event configured with
  * NS_PROPOSAL_DE_FLOW):
  *   q(u) on the unit cube: z0 = (logit(u) - mu) / sigma, then L RealNVP affine coupling

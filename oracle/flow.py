@@ -1,6 +1,6 @@
 """Normalising-flow proposal for the acceptance walk, and its maximum-likelihood training.
 
-The paper (Sec. 6) motivates flow-accelerated nested sampling (Nessai; Prathaban et al.) as a
+The paper (Sec. 5) motivates flow-accelerated nested sampling (Nessai; Prathaban et al.) as a
 natural fit for a batched GPU sampler but specifies no architecture.  Every choice below is a
 reading, kept deliberately plain:
 

@@ -17,7 +17,7 @@ One batch (iteration `it`) of the sampler:
      not printed -- parity unpinned);
   5. stop when ln(Z + L_max X) - ln Z < dlogZ (Sec. 4.1.1), or, for the fractional rule,
      when the live evidence L_mean X is below the given fraction of Z (Sec. 4.2).
-With a flow (p_flow > 0; the paper only motivates flows, Sec. 6): the flow starts from
+With a flow (p_flow > 0; the paper only motivates flows, Sec. 5): the flow starts from
 oracle.flow.init_flow and, in every batch it % flow_every == 0, after the deletion, is
 re-standardised and trained for flow_epochs full-batch Adam steps on the n_live - k
 survivors, which sample the prior above the new L* that the walks target (warm start:

@@ -1,7 +1,7 @@
 // flow.cuh -- the normalising-flow proposal's device data and the one-point density that the
 // walk evaluates on CUDA cores.
 //
-// The flow (a reading: the paper only motivates flow proposals, Sec. 6) is an L-layer
+// The flow (a reading: the paper only motivates flow proposals, Sec. 5) is an L-layer
 // RealNVP affine-coupling flow (Dinh, Sohl-Dickstein & Bengio 2017) on the unit cube:
 //   z0 = (logit(u) - mu) / sigma;  layer l conditions on the dimensions d with (d + l) even:
 //   a = m_l z, h1 = tanh(W1 a + b1), h2 = tanh(W2 h1 + b2), [s_raw | t] = W3 h2 + b3,
