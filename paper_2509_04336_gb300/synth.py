@@ -284,6 +284,29 @@ def priors_with_injection(w: Workload, ev: Event) -> list:
     return out
 
 
+def injection_set(n: int = 96, seed: int = 500, base: str = "four_param_2det_taylorf2", n_live: int = 300,
+                  naccept: int = 30, snr: float = 15.0, precision: int = PREC_MIXED_FF) -> list:
+    """Seeded injection study on synthetic data (the paper's PP test, Sec. 4.2, with a new set).
+
+    Injection e takes the base workload and redraws every sampled parameter from its own prior
+    (so that the true values follow the prior the sampler uses), keeps the fixed ones, adds
+    seeded noise (seed `seed` + e) and rescales the distance to network SNR `snr`.
+    """
+    rng = np.random.Generator(np.random.Philox(key=np.array([seed, 5555], dtype=np.uint64)))
+    w0 = workload(base)
+    out = []
+    for e in range(n):
+        inj = w0.injection.copy()
+        for i, p in enumerate(w0.priors):
+            if p.kind == UNIFORM:
+                inj[i] = rng.uniform(p.lo, p.hi)
+            elif p.kind != FIXED:
+                raise ValueError("injection_set draws uniform priors only")
+        out.append(replace(w0, name=f"injection_{e}", injection=inj, snr=snr, noise=True, seed=seed + e,
+                           n_live=n_live, num_delete=n_live // 2, naccept=naccept, precision=precision))
+    return out
+
+
 def batched_workloads(n_events: int = 64, seed: int = 100, waveform: int = PHENOMD_FORM,
                       precision: int = PREC_MIXED_FF) -> list:
     """Seeded population of independent events sampled together in one launch.
