@@ -246,13 +246,15 @@ def make_event(w: Workload,
                inner: Callable[[np.ndarray, np.ndarray, np.ndarray, float], float],
                event_index: int = 0,
                injection: np.ndarray | None = None,
-               snr: float | None = None) -> Event:
+               snr: float | None = None,
+               rescale: bool = True) -> Event:
     """Build one event: seeded noise plus an injected signal rescaled to the target SNR.
 
     `project(event, det, theta)` returns the detector strain of the caller's waveform
     model; `inner(a, b, psd, df)` the caller's noise-weighted inner product.  The
     distance of the injection is rescaled so that the network optimal SNR equals
-    the target (the strain amplitude is inversely proportional to distance).
+    the target (the strain amplitude is inversely proportional to distance); with
+    rescale=False the injection keeps its distance.
     """
     f = frequencies(w.f_min, w.df, w.n_bins)
     psd = analytic_psd(f)
@@ -267,7 +269,8 @@ def make_event(w: Workload,
     for i, d in enumerate(dets):
         h = project(ev, i, theta)
         snr2 += inner(h, h, d.psd, w.df)
-    theta[4] *= math.sqrt(snr2) / target
+    if rescale:
+        theta[4] *= math.sqrt(snr2) / target
     ev.theta_inj = theta
     for i, d in enumerate(dets):
         h = project(ev, i, theta)
