@@ -225,6 +225,60 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- ours
+def run_to_logz(gwns, w, ev, precision, device):
+    """Wall time from ns_init (host inputs) to ns_evidence of one event sampled to its stopping
+    rule, with the evidence it returns."""
+    import torch
+    cfg = gwns.make_config(w, synth.priors_with_injection(w, ev), precision=precision)
+    keep = gwns.make_event(ev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = gwns.ns_init([cfg], [keep[0]], device)
+    try:
+        done, batches = False, 0
+        while not done and batches < 4000:
+            _, prog = gwns.ns_step(h, 8)
+            batches += 8
+            done = bool(prog[0]["done"])
+        lz, lz_err, _, n_like = gwns.ns_evidence(h, 0)
+    finally:
+        gwns.ns_free(h)
+    return {"seconds": time.perf_counter() - t0, "log_z": lz, "log_z_err": lz_err, "n_like": int(n_like),
+            "iterations": int(prog[0]["iterations"]), "done": done}
+
+
+def time_to_logz(gwns, device):
+    """The metric's first half: wall time to ln Z, the evidence within 0.1 of the FP64 reference.
+
+    4-parameter configuration (2 detectors, 1969 bins, zero noise, 100 live points, seed 0):
+    the oracle's own run on the same seed is stored in tests/golden/logz_oracle.json (written by
+    tests/golden/make_logz_golden.py, which calls only oracle/); the library's FP64 walk
+    reproduces that chain (tests/test_gpu_walk.py), the float-float mode follows it up to
+    decisions within its lnL tolerance of L*.  11-parameter headline configuration: the
+    reference is the library's plain FP64 walk on the same data; the oracle itself would take
+    days at this size.  Events are made with the library's waveform.
+    """
+    out = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "logz_oracle.json")) as f:
+        golden = json.load(f)["four_param_2det_taylorf2"]
+    w4, ev4 = library_event(synth.workload("four_param_2det_taylorf2"), 0, device)
+    for tag, prec in (("fp64", synth.PREC_FP64), ("float_float", synth.PREC_MIXED_FF)):
+        r = run_to_logz(gwns, w4, ev4, prec, device)
+        d = abs(r["log_z"] - golden["log_z"])
+        out["four_param_2det_taylorf2_" + tag] = dict(r, reference="oracle (FP64 CPU, 1 core), same seed",
+                                                      reference_log_z=golden["log_z"],
+                                                      reference_seconds=golden["seconds"],
+                                                      abs_delta=d, within_0_1=d <= 0.1)
+    w11, ev11 = library_event(synth.workload(WORKLOAD), 0, device)
+    r = run_to_logz(gwns, w11, ev11, synth.PREC_MIXED_FF, device)
+    ref = run_to_logz(gwns, w11, ev11, synth.PREC_FP64, device)
+    d = abs(r["log_z"] - ref["log_z"])
+    out[WORKLOAD + "_float_float"] = dict(r, reference="plain FP64 walk on the GPU, same seed and data",
+                                          reference_log_z=ref["log_z"], reference_seconds=ref["seconds"],
+                                          abs_delta=d, within_0_1=d <= 0.1)
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -379,6 +433,7 @@ def run_ours(args):
     achieved = bins_evaluated * (FP32_FLOPS_PER_WALKER_BIN if w.waveform == synth.TAYLORF2
                                  else FP32_FLOPS_PER_WALKER_BIN_PD) / (mixed["walk_ms"] * 1e-3) / 1e12
     cpu_rate, cpu_info = oracle_walk_rate(w, ev, budget_s=args.cpu_seconds)
+    to_logz = time_to_logz(gwns, local) if (rank == 0 and args.workload == WORKLOAD) else None
     fp32_flops = FP32_FLOPS_PER_WALKER_BIN if w.waveform == synth.TAYLORF2 else FP32_FLOPS_PER_WALKER_BIN_PD
     clocks = mixed["clocks"] or {}
     line = {
@@ -414,6 +469,7 @@ def run_ours(args):
                          "sample": cpu_info["sample"]},
         "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
                    "reasons": clocks.get("reasons", [])},
+        "time_to_logz": to_logz,
     }
     print(json.dumps(line))
     if dist is not None:
