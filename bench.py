@@ -215,8 +215,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "kernel": "oracle acceptance walk (numpy FP64, CPU)",
-                       "step": "4 walkers x 8 DE steps of the oracle walk"},
+            "config": {"workload": WORKLOAD_DESCRIPTIONS[WORKLOAD], "precision": "FP64 (the oracle, numpy, CPU)",
+                       "step": "a bounded sample of the workload's walk: 4 walkers x 8 DE steps of the oracle",
+                       "events_per_rank": 1},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "per step: 4 walkers x 8 DE steps, bbh11_3det_4s_taylorf2 event"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
