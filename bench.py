@@ -226,11 +226,12 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- ours
-def run_to_logz(gwns, w, ev, precision, device):
+def run_to_logz(gwns, w, ev, precision, device, **cfg_kw):
     """Wall time from ns_init (host inputs) to ns_evidence of one event sampled to its stopping
-    rule, with the evidence it returns."""
+    rule, with the evidence it returns and the posterior's effective sample size
+    (Kish: 1 / sum w_i^2 of the normalised weights of the dead and final live points)."""
     import torch
-    cfg = gwns.make_config(w, synth.priors_with_injection(w, ev), precision=precision)
+    cfg = gwns.make_config(w, synth.priors_with_injection(w, ev), precision=precision, **cfg_kw)
     keep = gwns.make_event(ev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -242,10 +243,27 @@ def run_to_logz(gwns, w, ev, precision, device):
             batches += 8
             done = bool(prog[0]["done"])
         lz, lz_err, _, n_like = gwns.ns_evidence(h, 0)
+        seconds = time.perf_counter() - t0
+        _, lw = gwns.ns_posterior(h, 0)
     finally:
         gwns.ns_free(h)
-    return {"seconds": time.perf_counter() - t0, "log_z": lz, "log_z_err": lz_err, "n_like": int(n_like),
-            "iterations": int(prog[0]["iterations"]), "done": done}
+    wgt = np.exp(lw - np.max(lw))
+    wgt /= wgt.sum()
+    ess = float(1.0 / np.sum(wgt * wgt))
+    return {"seconds": seconds, "log_z": lz, "log_z_err": lz_err, "n_like": int(n_like),
+            "iterations": int(prog[0]["iterations"]), "done": done, "posterior_ess": ess,
+            "lnl_evals_per_ess": int(n_like) / ess}
+
+
+def flow_to_logz(gwns, w, ev, device, p_flows=(0.0, 0.5, 0.9)):
+    """The learned-proposal configuration's metrics: time to ln Z and likelihood calls per
+    effective posterior sample, for the DE walk (p_flow 0) and the DE + flow walk, each run
+    from ns_init to its stopping rule in the float-float mode."""
+    out = {}
+    for pf in p_flows:
+        kw = {} if pf == 0.0 else {"p_flow": pf, "flow_layers": 8}
+        out[str(pf)] = run_to_logz(gwns, w, ev, synth.PREC_MIXED_FF, device, **kw)
+    return out
 
 
 def time_to_logz(gwns, device):
@@ -435,6 +453,8 @@ def run_ours(args):
                                  else FP32_FLOPS_PER_WALKER_BIN_PD) / (mixed["walk_ms"] * 1e-3) / 1e12
     cpu_rate, cpu_info = oracle_walk_rate(w, ev, budget_s=args.cpu_seconds)
     to_logz = time_to_logz(gwns, local) if (rank == 0 and args.workload == WORKLOAD) else None
+    if rank == 0 and flow_run and args.to_logz:
+        to_logz = flow_to_logz(gwns, w, ev, local)
     fp32_flops = FP32_FLOPS_PER_WALKER_BIN if w.waveform == synth.TAYLORF2 else FP32_FLOPS_PER_WALKER_BIN_PD
     clocks = mixed["clocks"] or {}
     line = {
@@ -510,6 +530,8 @@ def main():
                     help="run this many batches of the workload without timing (a small case for ncu)")
     ap.add_argument("--precision", type=int, default=synth.PREC_MIXED_FF)
     ap.add_argument("--p-flow", type=float, default=0.5, help="flow-step probability of the *_flow workloads")
+    ap.add_argument("--to-logz", action="store_true",
+                    help="*_flow workloads: also run p_flow 0, 0.5, 0.9 to their stopping rule (minutes)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCRIPTIONS),
                     help="bench workload (the default is the headline line)")
     args = ap.parse_args()
