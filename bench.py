@@ -45,7 +45,7 @@ FP32_FLOPS_PER_WALKER_BIN = 243.0
 # power update (6): 76 + 3 * 49.
 FP32_FLOPS_PER_WALKER_BIN_PD = 223.0
 FP32_PEAK_TFLOPS = 80.5      # nominal GB300 FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz
-# DRAM bytes (read + write) of one walk launch, from one ncu capture of this build's kernel
+# DRAM bytes (read + write) of one walk launch, from one ncu capture of the current kernel
 # (walk_kernel_ff<3, WF>, batch 10 of the 4 s TaylorF2 workload and batch 3 of the 8 s
 # IMRPhenomD one); None for workloads without a capture of the current kernel.
 NCU_WALK_TRAFFIC_BYTES = {"bbh11_3det_4s_taylorf2": 246016 + 0, "bbh11_3det_8s_phenomd": 1646848 + 98560}

@@ -13,7 +13,7 @@ Each of the W walkers runs n_steps steps in the unit hypercube.  At step t walke
 The Philox key is (seed, event).  Returns the final positions, their ln L, the
 accepted-step counts and the number of likelihood calls of each walker.
 
-Flow steps (survey rows a11/a12; the paper only motivates flows, Sec. 5): with a flow q
+Flow steps (the paper only motivates flows, Sec. 5): with a flow q
 (oracle.flow) and probability p_flow, step t is instead an independence proposal
 u' = F^-1(x), x ~ N(0, I) (oracle.flow.base_normals, flow_step_draws).  It is accepted iff
 ln U < ln q(u) - ln q(u') and ln L(u') > ln L*, a Metropolis-Hastings step for the uniform

@@ -1,5 +1,5 @@
 // nested.cu -- batched nested sampling on the device (Sec. 2.2.1, Sec. 2.2.3, Sec. 3.1,
-// Sec. 3.2, Sec. 3.2.1) and the driver entry points ns_step, ns_evidence, ns_posterior,
+// Sec. 3.2, Sec. 3.2.1) and the sampler entry points ns_step, ns_evidence, ns_posterior,
 // ns_state_save and ns_state_load.
 //
 // One batch is three kernels that read and write the device-resident NsState:
