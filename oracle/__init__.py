@@ -17,6 +17,7 @@ Modules and the passages they follow:
   walk        DE acceptance walk under L > L* (Sec. 3.1, footnote on the DE scale)
   nested      batched nested sampling, expected shrinkage and evidence (Sec. 2.2.3, Sec. 3.2, Sec. 3.2.1)
   flow        affine-coupling flow proposal and its Adam training (motivated in Sec. 5; RealNVP)
+  relbin      relative-binning (heterodyned) likelihood (named in Sec. 3.3, Sec. 5; Zackay et al. 2018)
 
 Functions without an independent pin say "parity unpinned" in their docstring.
 """

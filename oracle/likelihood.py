@@ -14,12 +14,12 @@ from paper_2509_04336_gb300.synth import TAYLORF2, PHENOMD_FORM, frequencies
 from . import detector, taylorf2
 
 
-def polarizations(waveform: int, f, theta, table=None):
+def polarizations(waveform: int, f, theta, table=None, cutoff: bool = True):
     if waveform == TAYLORF2:
-        return taylorf2.polarizations(f, theta)
+        return taylorf2.polarizations(f, theta, cutoff)
     if waveform == PHENOMD_FORM:
         from . import phenomd
-        return phenomd.polarizations(f, theta, table)
+        return phenomd.polarizations(f, theta, table, cutoff)
     raise ValueError(waveform)
 
 
@@ -27,11 +27,14 @@ def inner(a, b, psd, df) -> float:
     return float(4.0 * df * np.sum((np.conj(a) * b).real / psd))
 
 
-def project(event, det_index: int, theta, waveform: int = TAYLORF2, table=None) -> np.ndarray:
-    """Strain of the waveform seen by one detector of the event."""
+def project(event, det_index: int, theta, waveform: int = TAYLORF2, table=None, f=None,
+            cutoff: bool = True) -> np.ndarray:
+    """Strain of the waveform seen by one detector of the event (at the event's bins, or at
+    the frequencies f; cutoff=False continues the template above its cutoff)."""
     d = event.detectors[det_index]
-    f = frequencies(event.f_min, event.df, event.n_bins)
-    hp, hc = polarizations(waveform, f, theta, table)
+    if f is None:
+        f = frequencies(event.f_min, event.df, event.n_bins)
+    hp, hc = polarizations(waveform, f, theta, table, cutoff)
     ra, dec, psi = float(theta[9]), float(theta[10]), float(theta[6])
     fp, fc = detector.antenna_pattern(d.x_arm, d.y_arm, ra, dec, psi, event.gmst)
     dt = detector.time_delay(d.vertex, ra, dec, event.gmst)

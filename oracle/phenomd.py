@@ -198,13 +198,16 @@ def phase_and_amplitude(f, theta, table=None):
     return psi, amp, on
 
 
-def polarizations(f, theta, table=None):
-    """(h+, hx) [1/Hz]: K f^(-7/6) a(f) with the TaylorF2 normalisation and polarisation factors."""
+def polarizations(f, theta, table=None, cutoff: bool = True):
+    """(h+, hx) [1/Hz]: K f^(-7/6) a(f) with the TaylorF2 normalisation and polarisation factors;
+    cutoff=False continues the merger-ringdown form above Mf = x_cut."""
     mc, q, chi1, chi2, dist, iota, _psi, phic, tc = (float(v) for v in theta[:9])
     f = np.asarray(f, dtype=np.float64)
     psi_pn, shape, on = phase_and_amplitude(f, theta, table)
     psi_f = 2.0 * PI * f * tc - 2.0 * phic - PI / 4.0 + psi_pn
-    amp = np.where(on, taylorf2.amplitude(f, mc, dist) * shape, 0.0)
+    amp = taylorf2.amplitude(f, mc, dist) * shape
+    if cutoff:
+        amp = np.where(on, amp, 0.0)
     ci = math.cos(iota)
     e = np.exp(-1j * psi_f)
     return amp * 0.5 * (1.0 + ci * ci) * e, -1j * amp * ci * e

@@ -87,13 +87,15 @@ def amplitude(f, mc: float, dist_mpc: float) -> np.ndarray:
     return math.sqrt(5.0 / 24.0) * PI ** (-2.0 / 3.0) * mc_s ** (5.0 / 6.0) * np.asarray(f, dtype=np.float64) ** (-7.0 / 6.0) / d_s
 
 
-def polarizations(f, theta):
-    """(h+, hx) [1/Hz] at frequencies f for the physical parameters theta [11]."""
+def polarizations(f, theta, cutoff: bool = True):
+    """(h+, hx) [1/Hz] at frequencies f for the physical parameters theta [11]; cutoff=False
+    continues the formula above f_cut (a smooth reference for relative binning)."""
     mc, q, chi1, chi2, dist, iota, _psi, phic, tc = (float(x) for x in theta[:9])
     f = np.asarray(f, dtype=np.float64)
     psi_f = 2.0 * PI * f * tc - 2.0 * phic - PI / 4.0 + pn_phase(f, mc, q, chi1, chi2)
     amp = amplitude(f, mc, dist)
-    amp = np.where(f <= cutoff_frequency(mc, q), amp, 0.0)
+    if cutoff:
+        amp = np.where(f <= cutoff_frequency(mc, q), amp, 0.0)
     ci = math.cos(iota)
     e = np.exp(-1j * psi_f)
     hp = amp * 0.5 * (1.0 + ci * ci) * e

@@ -1,0 +1,83 @@
+"""Pins of the relative-binning oracle (oracle/relbin.py) against the full likelihood."""
+import numpy as np
+import pytest
+
+from oracle import likelihood as L, prior as P, relbin
+from paper_2509_04336_gb300 import synth
+
+from _util import event, priors
+
+
+def _draws(w, ev, n, seed):
+    pri = priors(w, ev)
+    return [P.transform(x, pri) for x in synth.uniform_unit_cube(n, w.n_dim, seed)]
+
+
+def test_edges_cover_the_grid_and_scale_with_eps():
+    w, ev = event("bbh11_3det_4s_taylorf2")
+    e1 = relbin.default_edges(ev.f_min, ev.df, ev.n_bins, eps=0.25)
+    e2 = relbin.default_edges(ev.f_min, ev.df, ev.n_bins, eps=2.0)
+    for e in (e1, e2):
+        assert e[0] == 0 and e[-1] == ev.n_bins and np.all(np.diff(e) >= 1)
+    assert 10 < len(e2) < len(e1) < ev.n_bins // 20
+
+
+@pytest.mark.parametrize("name", ["bbh11_3det_4s_taylorf2", "bbh11_3det_8s_phenomd"])
+def test_one_grid_bin_per_coarse_bin_is_the_full_likelihood(name):
+    # With every coarse bin one grid bin wide, the linear term vanishes and the expansion is
+    # exact: the relative-binning ln L equals the full one for any parameters.
+    w, ev = event(name, f_max=200.0) if "phenomd" in name else event(name)
+    edges = np.arange(ev.n_bins + 1)
+    sd = relbin.summary_data(ev, ev.theta_inj, edges, w.waveform)
+    for th in _draws(w, ev, 4, 3):
+        want = L.log_likelihood(ev, th, w.waveform)
+        assert abs(relbin.log_likelihood(ev, th, sd, w.waveform) - want) <= 1e-9 * abs(want)
+
+
+@pytest.mark.parametrize("name", ["bbh11_3det_4s_taylorf2", "bbh11_3det_8s_phenomd"])
+def test_fiducial_point_is_exact(name):
+    # At theta0 the ratio is 1 at every edge: the summary data sum the full likelihood.
+    w, ev = event(name)
+    edges = relbin.default_edges(ev.f_min, ev.df, ev.n_bins)
+    sd = relbin.summary_data(ev, ev.theta_inj, edges, w.waveform)
+    want = L.log_likelihood(ev, ev.theta_inj, w.waveform)
+    assert abs(relbin.log_likelihood(ev, ev.theta_inj, sd, w.waveform) - want) <= 1e-9 * abs(want)
+    assert abs(relbin.log_likelihood(ev, ev.theta_inj, sd, w.waveform, use_ratio=True)
+               - L.log_likelihood(ev, ev.theta_inj, w.waveform, use_ratio=True)) <= 1e-6
+
+
+def test_frequency_independent_ratio_is_exact():
+    # Distance and inclination change only the constant factor of h / h0 (the cutoff stays
+    # put), so the linear expansion is exact whatever the bins.
+    w, ev = event("bbh11_3det_4s_taylorf2")
+    edges = relbin.default_edges(ev.f_min, ev.df, ev.n_bins, eps=3.0)
+    sd = relbin.summary_data(ev, ev.theta_inj, edges, w.waveform)
+    th = ev.theta_inj.copy()
+    th[4] *= 1.7
+    th[5] = 1.1
+    want = L.log_likelihood(ev, th, w.waveform)
+    assert abs(relbin.log_likelihood(ev, th, sd, w.waveform) - want) <= 1e-9 * abs(want)
+
+
+@pytest.mark.parametrize("name", ["bbh11_3det_4s_taylorf2", "bbh11_3det_8s_phenomd"])
+def test_close_to_the_full_likelihood_in_the_posterior_bulk(name):
+    # Random points around theta0, shrunk until the full ln L is within 30 of its value at
+    # theta0 (the bulk of the posterior): the compressed ln L stays within 0.05 of the full one.
+    w, ev = event(name)
+    edges = relbin.default_edges(ev.f_min, ev.df, ev.n_bins)
+    sd = relbin.summary_data(ev, ev.theta_inj, edges, w.waveform)
+    l0 = L.log_likelihood(ev, ev.theta_inj, w.waveform)
+    rng = np.random.default_rng(4)
+    scale = np.array([1e-2 * ev.theta_inj[0], 0.02, 0.02, 0.02, 50.0, 0.05, 0.05, 0.05, 2e-4, 0.02, 0.02])
+    worst = 0.0
+    for _ in range(6):
+        step = scale * rng.normal(size=11)
+        while True:
+            th = ev.theta_inj + step
+            want = L.log_likelihood(ev, th, w.waveform)
+            if want > l0 - 30.0:
+                break
+            step *= 0.5
+        got = relbin.log_likelihood(ev, th, sd, w.waveform)
+        worst = max(worst, abs(got - want))
+    assert worst < 0.05, worst
