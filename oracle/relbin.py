@@ -18,8 +18,10 @@ strain only at the coarse-bin edges (~10^2 instead of ~10^4 bins).
 
 The template's cutoff (f_ISCO for TaylorF2, Mf = 0.2 for the IMRPhenomD form) moves with the
 proposal's mass and makes r discontinuous.  Coarse bins wholly below the proposal's cutoff use
-the expansion (the edge values of r are taken from the continued template); the coarse bin that
-holds the cutoff is summed exactly over its active bins; coarse bins above it contribute nothing.
+the expansion (the edge values of r are taken from the continued template), except the last
+coarse bin of the grid, whose right edge lies off the grid; from the first coarse bin that does
+not qualify up to the cutoff, the active bins are summed exactly (that range holds the cutoff,
+or it is the last coarse bin); the bins above the cutoff contribute nothing.
 """
 from __future__ import annotations
 
@@ -100,6 +102,15 @@ def active_bins(event, theta, waveform: int, table=None) -> int:
     return n
 
 
+def n_expanded(edges, k_end: int, n_bins: int) -> int:
+    """Number of leading coarse bins taken by the expansion: those wholly below the cutoff
+    (right edge <= k_end) whose right edge is a grid bin (< n_bins)."""
+    n = 0
+    while n + 1 < len(edges) and edges[n + 1] <= k_end and edges[n + 1] < n_bins:
+        n += 1
+    return n
+
+
 def log_likelihood(event, theta, sd: dict, waveform: int, use_ratio: bool = False, table=None) -> float:
     """ln L of theta from the summary data sd (the -1/2 <d - h|d - h> of the full likelihood,
     or the ratio form)."""
@@ -109,22 +120,22 @@ def log_likelihood(event, theta, sd: dict, waveform: int, use_ratio: bool = Fals
     f = frequencies(event.f_min, event.df, event.n_bins)
     dh = 0.0
     hh = 0.0
+    n_full = n_expanded(edges, k_end, event.n_bins)
+    lo = int(edges[n_full])
     for i, d in enumerate(event.detectors):
-        r = L.project(event, i, theta, waveform, table, f=fe, cutoff=False) / sd["h0_edges"][i]
+        r = L.project(event, i, theta, waveform, table, f=fe[:n_full + 1], cutoff=False) / sd["h0_edges"][i][:n_full + 1]
         w = 4.0 * event.df / d.psd
-        for b in range(nb):
-            lo, hi = int(edges[b]), int(edges[b + 1])
-            if hi <= k_end:
-                r0 = r[b]
-                r1 = (r[b + 1] - r[b]) / (fe[b + 1] - fe[b])
-                dh += (sd["A0"][i, b] * r0 + sd["A1"][i, b] * r1).real
-                hh += (sd["B0"][i, b] * abs(r0) ** 2 + 2.0 * sd["B1"][i, b] * (np.conj(r0) * r1).real
-                       + sd["B2"][i, b] * abs(r1) ** 2)
-            elif lo < k_end:
-                # the coarse bin that holds the cutoff: exact over its active bins
-                h = L.project(event, i, theta, waveform, table, f=f[lo:k_end])
-                dh += float(np.sum((np.conj(d.data[lo:k_end]) * h).real * w[lo:k_end]))
-                hh += float(np.sum(np.abs(h) ** 2 * w[lo:k_end]))
+        for b in range(n_full):
+            r0 = r[b]
+            r1 = (r[b + 1] - r[b]) / (fe[b + 1] - fe[b])
+            dh += (sd["A0"][i, b] * r0 + sd["A1"][i, b] * r1).real
+            hh += (sd["B0"][i, b] * abs(r0) ** 2 + 2.0 * sd["B1"][i, b] * (np.conj(r0) * r1).real
+                   + sd["B2"][i, b] * abs(r1) ** 2)
+        if lo < k_end:
+            # from the first coarse bin not expanded up to the cutoff: exact over the active bins
+            h = L.project(event, i, theta, waveform, table, f=f[lo:k_end])
+            dh += float(np.sum((np.conj(d.data[lo:k_end]) * h).real * w[lo:k_end]))
+            hh += float(np.sum(np.abs(h) ** 2 * w[lo:k_end]))
     if use_ratio:
         return dh - 0.5 * hh
     return -0.5 * (sd["dd"] - 2.0 * dh + hh)
