@@ -226,10 +226,12 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- ours
-def run_to_logz(gwns, w, ev, precision, device, **cfg_kw):
+def run_to_logz(gwns, w, ev, precision, device, relbin_edges=None, **cfg_kw):
     """Wall time from ns_init (host inputs) to ns_evidence of one event sampled to its stopping
     rule, with the evidence it returns and the posterior's effective sample size
-    (Kish: 1 / sum w_i^2 of the normalised weights of the dead and final live points)."""
+    (Kish: 1 / sum w_i^2 of the normalised weights of the dead and final live points).
+    relbin_edges: coarse-bin edges of the relative-binning likelihood around the injection
+    (its setup, ns_relbin_set, inside the timed region)."""
     import torch
     cfg = gwns.make_config(w, synth.priors_with_injection(w, ev), precision=precision, **cfg_kw)
     keep = gwns.make_event(ev)
@@ -237,6 +239,8 @@ def run_to_logz(gwns, w, ev, precision, device, **cfg_kw):
     t0 = time.perf_counter()
     h = gwns.ns_init([cfg], [keep[0]], device)
     try:
+        if relbin_edges is not None:
+            gwns.ns_relbin_set(h, 0, relbin_edges, ev.theta_inj)
         done, batches = False, 0
         while not done and batches < 4000:
             _, prog = gwns.ns_step(h, 8)
@@ -519,6 +523,72 @@ def run_profile_case(args):
     return 0
 
 
+def run_relbin(args):
+    """Relative-binning line: the float-float walk on the full likelihood and on the
+    relative-binning likelihood (coarse bins of eps radians), each timed over K sampler
+    batches after W warm-up batches (lnL evals/s, L2 flushed between batches), then each run
+    from ns_init to its stopping rule (wall time to ln Z and the evidence)."""
+    import torch
+
+    from paper_2509_04336_gb300 import build, gwns, relbin
+
+    rank, world, local = rank_info()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    build.build()
+    gwns.load()
+    w, ev = library_event(synth.workload(args.workload), 0, local)
+    edges = relbin.coarse_edges(ev.f_min, ev.df, ev.n_bins, args.relbin)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    arms = {}
+    with ClockSampler(local) as clocks:
+        for tag, ed in (("full", None), ("relbin", edges)):
+            h = gwns.ns_init([gwns.make_config(w, synth.priors_with_injection(w, ev),
+                                               precision=synth.PREC_MIXED_FF)], [ev], local)
+            try:
+                if ed is not None:
+                    gwns.ns_relbin_set(h, 0, ed, ev.theta_inj)
+                for _ in range(args.warmup):
+                    gwns.ns_step(h, 1)
+                _, p0 = gwns.ns_step(h, 0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ms = 0.0
+                for _ in range(args.steps):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    e0.record()
+                    _, p = gwns.ns_step(h, 1)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                evals = p[0]["n_like"] - p0[0]["n_like"]
+                arms[tag] = {"lnl_evals_per_s": evals / (ms * 1e-3), "ms_per_step": ms / args.steps,
+                             "walk_ms_per_step": (p[0]["walk_ms"] - p0[0]["walk_ms"]) / args.steps,
+                             "spec_depth": p[0]["spec_depth"], "mean_walk_steps": p[0]["n_steps"]}
+            finally:
+                gwns.ns_free(h)
+    for tag, ed in (("full", None), ("relbin", edges)):
+        arms[tag]["to_logz"] = run_to_logz(gwns, w, ev, synth.PREC_MIXED_FF, local, relbin_edges=ed)
+    ck = clocks.summary()
+    line = {
+        "metric": "relative-binning likelihood: lnL evals/s and wall time to ln Z against the full likelihood",
+        "value": arms["relbin"]["lnl_evals_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": arms["relbin"]["ms_per_step"], "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESCRIPTIONS[args.workload], "relbin_eps_rad": args.relbin,
+                   "coarse_bins": int(len(edges) - 1), "fiducial": "the injection",
+                   "precision": "float-float phase (mode 2)", "l2": "flushed (256 MB write) between timed steps"},
+        "full": arms["full"], "relbin": arms["relbin"],
+        "speedup_evals": arms["relbin"]["lnl_evals_per_s"] / arms["full"]["lnl_evals_per_s"],
+        "speedup_to_logz": arms["full"]["to_logz"]["seconds"] / arms["relbin"]["to_logz"]["seconds"],
+        "abs_delta_log_z": abs(arms["full"]["to_logz"]["log_z"] - arms["relbin"]["to_logz"]["log_z"]),
+        "clocks": {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons", [])},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -534,7 +604,16 @@ def main():
                     help="*_flow workloads: also run p_flow 0, 0.5, 0.9 to their stopping rule (minutes)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCRIPTIONS),
                     help="bench workload (the default is the headline line)")
+    ap.add_argument("--relbin", type=float, default=0.0,
+                    help="eps [rad] > 0: the relative-binning line (full vs relative-binning likelihood) "
+                         "on --workload instead of the headline line")
     args = ap.parse_args()
+    if args.relbin > 0.0:
+        if args.workload == "batched64":
+            ap.error("--relbin runs a single-event workload")
+        if args.warmup < 3:
+            ap.error("--warmup must be >= 3")
+        return run_relbin(args)
     if args.profile_batches > 0:
         return run_profile_case(args)
     if args.warmup < 3:

@@ -278,6 +278,25 @@ int ns_flow_grad(ns_handle* h, int event, const double* u, int n, float* grad, d
  * -ln q; losses [epochs] (may be NULL) receives the loss before each step. */
 int ns_flow_train(ns_handle* h, int event, const double* u, int n, int epochs, double* losses);
 
+/* ---- relative binning (Sec. 3.3 and Sec. 5: the likelihood compression for long signals;
+ * Zackay, Dai & Venumadhav 2018) ----
+ * Switches event `event` of an NS_PREC_MIXED_FF handle to the relative-binning likelihood.
+ * edges [n_edges]: host int32 grid-bin indices of the coarse-bin edges, strictly increasing,
+ * edges[0] = 0 and edges[n_edges - 1] = n_bins (the caller keeps ownership).  theta0 [11]:
+ * host, the fiducial parameters.  The fiducial template h0 is the template at theta0 continued
+ * above its cutoff; per coarse bin and detector the call computes (FP64, stored FP32) the
+ * summary data A0 = sum conj(d) h0 w, A1 = sum conj(d) h0 w x, B0, B1, B2 = sum |h0|^2 w x^{0,1,2}
+ * (w = 4 df / S_n, x = f - f_edge).  A proposal's ln L then takes r = h / h0 at the edges and,
+ * for every coarse bin wholly below its cutoff whose right edge is a grid bin,
+ * <d|h> = Re(A0 r + A1 r'), <h|h> = B0 |r|^2 + 2 B1 Re(conj(r) r') + B2 |r'|^2 (r' the slope
+ * between the edges); from the first other coarse bin up to the cutoff it sums the bins exactly.
+ * ns_likelihood_batch, ns_walk_batch and ns_step of the event use it from then on; n_edges = 0
+ * restores the full likelihood.  Call before the first ns_step of the event: the initial live
+ * points are re-evaluated.  The setting is not part of a checkpoint.
+ * Errors: NS_EINVAL (other precision, bad edges, after the first step, a fiducial that vanishes
+ * at an edge), NS_ENONFINITE (theta0 or the summary data), NS_ENOMEM, NS_ECUDA. */
+int ns_relbin_set(ns_handle* h, int event, const int32_t* edges, int n_edges, const double* theta0);
+
 void ns_free(ns_handle* h);
 const char* ns_last_error(ns_handle* h);
 

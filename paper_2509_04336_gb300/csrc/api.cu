@@ -282,6 +282,7 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
 }
 
 void free_event(EventHost& E) {
+  relbin_free(E);
   cudaFree(E.d_basis64);
   cudaFree(E.d_basis_ff);
   cudaFree(E.d_z64);

@@ -60,6 +60,10 @@ struct EventHost {
   double* d_gw64 = nullptr;
   float* d_gw32 = nullptr;
   float* d_hhp32 = nullptr;
+  int32_t* d_rb_edges = nullptr;   // relative binning (relbin.cu)
+  float2* d_rb_q0 = nullptr;
+  float2* d_rb_a = nullptr;
+  float4* d_rb_b = nullptr;
   NsState ns;            // host mirror of the device pointers and static fields
   FlowHost flow;         // flow proposal (enabled for NS_PROPOSAL_DE_FLOW)
 };
@@ -104,6 +108,7 @@ int ensure_scratch(ns_handle* h, gwns::Scratch& s, size_t bytes);
 int nested_init(ns_handle* h);
 int default_spec(int precision);
 void nested_free(ns_handle* h);
+void relbin_free(gwns::EventHost& E);
 // flow proposal (flow_api.cu)
 int flow_check_config(const ns_config& c, int e);
 int flow_setup(ns_handle* h, int e);

@@ -55,8 +55,9 @@ cudaError_t launch_unit_likelihood(int precision, int waveform, int n_det, const
                                    int n, double* d_lnl, cudaStream_t s);
 cudaError_t launch_unit_to_theta(const EventDev* d_ev, const double* d_u, int64_t n, double* d_theta,
                                  cudaStream_t s);
+// no_cutoff: continue the template above its cutoff (the relative-binning fiducial).
 cudaError_t launch_waveform(int waveform, int n_det, const EventDev* d_ev, const double* d_theta, int n, int n_bins,
-                            double* d_hre, double* d_him, cudaStream_t s);
+                            double* d_hre, double* d_him, cudaStream_t s, int no_cutoff = 0);
 // Block b walks walker blk_local[b] of task blk_task[b].
 cudaError_t launch_walk(int precision, int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
                         const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s);

@@ -90,6 +90,12 @@ struct EventDev {
   const float* hhp32;                  // [n_det][n_bins] hh_prefix * 2^-140 (FP32 range)
   float vc_f[kMaxDet][3][2];           // detector vertex / c [s]
   float fmin_f[2], df_f[2], gmst_f[2];
+  // relative binning (ns_relbin_set; rb_nb = 0: the full likelihood)
+  int rb_nb;                           // coarse bins
+  const int32_t* rb_edges;             // [rb_nb + 1] grid-bin edges, rb_edges[rb_nb] = n_bins
+  const float2* rb_q0;                 // [n_det][rb_nb] f^(-7/6) / (h0 2^70) at the edges
+  const float2* rb_a;                  // [n_det][rb_nb][2] summary data A0, A1
+  const float4* rb_b;                  // [n_det][rb_nb] summary data (B0, B1, B2, 0)
 };
 
 // The IMRPhenomD-form part of the per-walker constants (in cycles).

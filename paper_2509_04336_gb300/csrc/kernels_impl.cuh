@@ -259,6 +259,179 @@ __device__ inline double lnl_ff(const EventDev& ev, const WalkerParams& P, const
   return (double)l.h + (double)l.l;
 }
 
+// ---------------------------------------------------------------- relative binning
+// The float-float TaylorF2 phase at grid bin k [cycles, reduced to [-1/2, 1/2] plus a small
+// low part], as the first half of bin_accumulate_ff computes it.
+__device__ __forceinline__ float tf2_ff_r0(const EventDev& ev, const WalkerParams& p, int k) {
+  const float2* g = ev.basis_ff + k;
+  const size_t gs = (size_t)ev.n_bins;
+  float q[kBasis];
+  float sl = p.ph0l;
+#pragma unroll
+  for (int j = 0; j < kBasis; ++j) {
+    const float2 gj = g[j * gs];
+    q[j] = p.Ch[j] * gj.x;
+    float e = fmaf(p.Ch[j], gj.x, -q[j]);
+    e = fmaf(p.Ch[j], gj.y, e);
+    sl += fmaf(p.Cl[j], gj.x, e);
+  }
+#pragma unroll
+  for (int w = 1; w < kBasis; w <<= 1) {
+#pragma unroll
+    for (int j = 0; j + w < kBasis; j += 2 * w) {
+      const float t = q[j] + q[j + w];
+      const float bb = t - q[j];
+      sl += (q[j] - (t - bb)) + (q[j + w] - bb);
+      q[j] = t;
+    }
+  }
+  const float t = p.ph0h + q[0];
+  const float bb = t - p.ph0h;
+  sl += (p.ph0h - (t - bb)) + (q[0] - bb);
+  return (t - rintf(t)) + sl;
+}
+
+// The float-float IMRPhenomD-form phase [cycles] and amplitude shape at grid bin k, as the first
+// half of pd_accumulate_ff computes them.
+__device__ __forceinline__ void pd_ff_r0_amp(const EventDev& ev, const WalkerParams& p, const PhenomExtra& e,
+                                             int k, float& r0, float& amp) {
+  const float2* g = ev.basis_ff + k;
+  const size_t gs = (size_t)ev.n_bins;
+  const float ff = g[13 * gs].x;
+  float sh, sl, extra = 0.f;
+  if (k < e.k1) {
+    sh = p.ph0h; sl = p.ph0l;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) ff_term(sh, sl, p.Ch[j], p.Cl[j], g[j * gs]);
+    ff_term(sh, sl, e.Cxh[0], e.Cxl[0], g[8 * gs]);
+    ff_term(sh, sl, e.Cxh[1], e.Cxl[1], g[9 * gs]);
+    ff_term(sh, sl, e.Cxh[2], e.Cxl[2], g[10 * gs]);
+  } else if (k < e.k2) {
+    sh = e.ph0_int_h; sl = e.ph0_int_l;
+    ff_term(sh, sl, e.Cxh[3], e.Cxl[3], g[6 * gs]);
+    ff_term(sh, sl, e.Cxh[4], e.Cxl[4], g[11 * gs]);
+    ff_term(sh, sl, e.Cxh[5], e.Cxl[5], g[13 * gs]);
+  } else {
+    sh = e.ph0_mr_h; sl = e.ph0_mr_l;
+    ff_term(sh, sl, e.Cxh[6], e.Cxl[6], g[1 * gs]);
+    ff_term(sh, sl, e.Cxh[7], e.Cxl[7], g[12 * gs]);
+    ff_term(sh, sl, e.Cxh[8], e.Cxl[8], g[13 * gs]);
+    extra = e.at_scalef * atanf((e.Mf * ff - e.at_cf) * e.at_invf);
+  }
+  r0 = (sh - rintf(sh)) + sl + extra;
+  amp = pd_amp_f32(e, k, ff, g[4 * gs].x);
+}
+
+// ln L of one proposal with the relative-binning likelihood (mode 2), evaluated by one warp
+// (every lane returns it).  Coarse bins wholly below the proposal's cutoff whose right edge is
+// a grid bin take the linear expansion of r = h / h0 between their edges (31 bins a pass; lane
+// l holds edge base + l and reads its right neighbour by a shuffle); from the first other coarse
+// bin up to the cutoff the active bins are summed exactly with the per-bin bodies.
+template <int NDET, int WF>
+__device__ double rb_lnl_warp(const EventDev& ev, const WalkerParams& P, int lane) {
+  const int nb = ev.rb_nb;
+  const int32_t* E = ev.rb_edges;
+  const int k_end = P.k_end;
+  const int kmax = min(k_end, ev.n_bins - 1);
+  int lo = 0, hi = nb;   // n_full = the largest n with E[n] <= kmax (E[0] = 0)
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (E[mid] <= kmax) lo = mid;
+    else hi = mid - 1;
+  }
+  const int n_full = lo;
+  float dh = 0.f, dhc = 0.f, hh = 0.f, hhc = 0.f;
+  const float df = ev.df_f[0];
+  for (int base = 0; base < n_full; base += 31) {
+    const int ei = base + lane;
+    const bool have = ei <= n_full;
+    float rre[NDET], rim[NDET];
+#pragma unroll
+    for (int det = 0; det < NDET; ++det) { rre[det] = 0.f; rim[det] = 0.f; }
+    if (have) {
+      const int k = E[ei];
+      float r0, amp = 1.0f;
+      if (WF == 0) r0 = tf2_ff_r0(ev, P, k);
+      else pd_ff_r0_amp(ev, P, P.pd, k, r0, amp);
+      const float kf = (float)k;
+#pragma unroll
+      for (int det = 0; det < NDET; ++det) {
+        const float kb = kf * P.sbh[det];
+        float ph = (r0 + P.sa[det]) + (kb - rintf(kb)) + kf * P.sbl[det];
+        ph = ph - rintf(ph);
+        float sn, cs;
+        sincospif(2.0f * ph, &sn, &cs);
+        // h f^(7/6) 2^70 = amp (K P) exp(-2 pi i ph)
+        const float hre = amp * (P.kpf_re[det] * cs + P.kpf_im[det] * sn);
+        const float him = amp * (P.kpf_im[det] * cs - P.kpf_re[det] * sn);
+        const float2 q = ev.rb_q0[(size_t)det * nb + ei];
+        rre[det] = hre * q.x - him * q.y;
+        rim[det] = hre * q.y + him * q.x;
+      }
+    }
+    const int b = base + lane;
+    const bool bin = lane < 31 && b < n_full;
+    const float inv = bin ? 1.0f / ((float)(E[b + 1] - E[b]) * df) : 0.f;
+#pragma unroll
+    for (int det = 0; det < NDET; ++det) {
+      const float nre = __shfl_down_sync(0xffffffffu, rre[det], 1);
+      const float nim = __shfl_down_sync(0xffffffffu, rim[det], 1);
+      if (bin) {
+        const float r1re = (nre - rre[det]) * inv, r1im = (nim - rim[det]) * inv;
+        const float2 a0 = ev.rb_a[((size_t)det * nb + b) * 2];
+        const float2 a1 = ev.rb_a[((size_t)det * nb + b) * 2 + 1];
+        const float4 bq = ev.rb_b[(size_t)det * nb + b];
+        kahan_add(dh, dhc, a0.x * rre[det] - a0.y * rim[det] + a1.x * r1re - a1.y * r1im);
+        kahan_add(hh, hhc, bq.x * (rre[det] * rre[det] + rim[det] * rim[det]) +
+                               2.0f * bq.y * (rre[det] * r1re + rim[det] * r1im) +
+                               bq.z * (r1re * r1re + r1im * r1im));
+      }
+    }
+  }
+  // exact part: the active bins from the first coarse bin not expanded
+  const int kx = E[n_full];
+  double xdh = 0.0, xhh = 0.0;
+  if (WF == 0) {
+    AccF32 acc;
+    acc.zero();
+    for (int k = kx + lane; k < k_end; k += 32) bin_accumulate_ff<NDET>(ev, P, k, acc);
+    float sdh = 0.f;
+#pragma unroll
+    for (int det = 0; det < NDET; ++det)
+      sdh += P.kpf_re[det] * (acc.re[det] - acc.cre[det]) - P.kpf_im[det] * (acc.im[det] - acc.cim[det]);
+    xdh = ldexp((double)sdh, -kKpScaleExp);
+    if (lane == 0 && kx < k_end) {
+      float hsum = 0.f;
+      for (int det = 0; det < NDET; ++det) {
+        const float* pre = ev.hhp32 + (size_t)det * ev.n_bins;
+        const float seg = pre[k_end - 1] - (kx > 0 ? pre[kx - 1] : 0.f);
+        hsum += (P.kpf_re[det] * P.kpf_re[det] + P.kpf_im[det] * P.kpf_im[det]) * seg;
+      }
+      xhh = (double)hsum;
+    }
+  } else {
+    AccPD32 acc;
+    acc.zero();
+    for (int k = kx + lane; k < k_end; k += 32) pd_accumulate_ff<NDET>(ev, P, P.pd, k, acc);
+    float sdh = 0.f, shh = 0.f;
+#pragma unroll
+    for (int det = 0; det < NDET; ++det) {
+      sdh += P.kpf_re[det] * (acc.re[det] - acc.cre[det]) - P.kpf_im[det] * (acc.im[det] - acc.cim[det]);
+      shh += (P.kpf_re[det] * P.kpf_re[det] + P.kpf_im[det] * P.kpf_im[det]) * acc.hh[det];
+    }
+    xdh = ldexp((double)sdh, -kKpScaleExp);
+    xhh = (double)shh * (double)ev.hh_unscale_f;
+  }
+  double tdh = (double)dh - (double)dhc + xdh;
+  double thh = (double)hh - (double)hhc + xhh;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    tdh += __shfl_xor_sync(0xffffffffu, tdh, off);
+    thh += __shfl_xor_sync(0xffffffffu, thh, off);
+  }
+  return ev.use_ratio ? tdh - 0.5 * thh : -0.5 * (ev.dd_total - 2.0 * tdh + thh);
+}
+
 __device__ inline bool theta_ok(const double* th) {
   for (int i = 0; i < kParams; ++i) if (!isfinite(th[i])) return false;
   return th[0] > 0.0 && th[1] > 0.0 && th[4] > 0.0;
@@ -319,6 +492,22 @@ __global__ void __launch_bounds__(kThreads) likelihood_kernel(const EventDev* __
     else P.k_end = 0;
   }
   __syncthreads();
+  if constexpr (PREC == 2) {
+    if (ev.rb_nb > 0) {   // relative binning: warp 0 evaluates the proposal
+      if (threadIdx.x < 32) {
+        const double v = ok ? rb_lnl_warp<NDET, WF>(ev, P, threadIdx.x) : 0.0;
+        if (threadIdx.x == 0) {
+          if (ok) {
+            lnl[w] = v;
+          } else {
+            lnl[w] = __longlong_as_double(0x7ff8000000000000ll);
+            atomicOr(status, 1);
+          }
+        }
+      }
+      return;
+    }
+  }
   cta_sums<PREC, NDET, WF>(ev, P, red, vals);
   if (threadIdx.x == 0) {
     if (ok) {
@@ -343,6 +532,15 @@ __global__ void __launch_bounds__(kThreads) unit_likelihood_kernel(const EventDe
   const int w = blockIdx.x;
   if (threadIdx.x == 0) setup_from_unit<PREC, WF>(ev, u + (size_t)w * ev.n_dim, P);
   __syncthreads();
+  if constexpr (PREC == 2) {
+    if (ev.rb_nb > 0) {
+      if (threadIdx.x < 32) {
+        const double v = rb_lnl_warp<NDET, WF>(ev, P, threadIdx.x);
+        if (threadIdx.x == 0) lnl[w] = isfinite(v) ? v : -INFINITY;
+      }
+      return;
+    }
+  }
   cta_sums<PREC, NDET, WF>(ev, P, red, vals);
   if (threadIdx.x == 0) {
     double v = lnl_from_vals<PREC, NDET, WF>(ev, P, vals);
@@ -365,7 +563,8 @@ __global__ void unit_to_theta_kernel(const EventDev* __restrict__ evp, const dou
 template <int NDET, int WF>
 __global__ void __launch_bounds__(256) waveform_kernel(const EventDev* __restrict__ evp,
                                                        const double* __restrict__ theta, int n_bins,
-                                                       double* __restrict__ h_re, double* __restrict__ h_im) {
+                                                       double* __restrict__ h_re, double* __restrict__ h_im,
+                                                       int no_cutoff) {
   __shared__ WalkerParams P;
   const EventDev& ev = *evp;
   const int w = blockIdx.y;
@@ -373,6 +572,7 @@ __global__ void __launch_bounds__(256) waveform_kernel(const EventDev* __restric
     double th[kParams];
     for (int i = 0; i < kParams; ++i) th[i] = theta[(size_t)w * kParams + i];
     setup_from_theta<0, WF>(ev, th, P);
+    if (no_cutoff) P.k_end = n_bins;
   }
   __syncthreads();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -759,6 +959,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   __shared__ TF2Part parts[WF == 0 ? kSpecMax : 1];
   __shared__ int cstep[kSpecMax];
   __shared__ float part_sums[kSpecMax][2 * kMaxVals];
+  __shared__ double s_rbl[kSpecMax];   // relative binning: ln L of each proposal
   // IMRPhenomD form: every warp's compensated sums of every proposal
   __shared__ float wsums[WF == 1 ? kSpecMax : 1][kWarps][2 * kMaxVals];
   __shared__ double u[kMaxDim];
@@ -932,7 +1133,15 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
     // 3. likelihoods
     constexpr int V = Pow2Vals<NV>::value;
     constexpr int group = 32 / V;
-    if (WF == 1) {
+    const bool rb = ev.rb_nb > 0;
+    if (rb) {
+      // relative binning (~10^2 coarse-bin edges a proposal): a warp per proposal
+      for (int i = warp; i < nin; i += kWarps) {
+        const double v = rb_lnl_warp<NDET, WF>(ev, P[i], lane);
+        if (lane == 0) s_rbl[i] = v;
+      }
+      __syncthreads();
+    } else if (WF == 1) {
       // IMRPhenomD form (thousands of bins a proposal): the whole CTA on each proposal in turn,
       // so that proposals of different lengths leave no warp waiting; warp 0 combines the four
       // warps' compensated sums below
@@ -962,7 +1171,9 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
     if (warp == 0) {
       double l = 0.0;
       if (lane < nin) {
-        if (WF == 1) {
+        if (rb) {
+          l = s_rbl[lane];
+        } else if (WF == 1) {
           // (s, c) of the four warps, summed with error-free additions
           float ps[2 * NV];
 #pragma unroll

@@ -18,10 +18,10 @@ cudaError_t launch_unit_to_theta(const EventDev* d_ev, const double* d_u, int64_
 }
 
 cudaError_t launch_waveform(int waveform, int n_det, const EventDev* d_ev, const double* d_theta, int n, int n_bins,
-                            double* d_hre, double* d_him, cudaStream_t s) {
+                            double* d_hre, double* d_him, cudaStream_t s, int no_cutoff) {
   if (n <= 0) return cudaSuccess;
   dim3 grid((n_bins + 255) / 256, n);
-#define GWNS_WF(P_, N, W) waveform_kernel<N, W><<<grid, 256, 0, s>>>(d_ev, d_theta, n_bins, d_hre, d_him)
+#define GWNS_WF(P_, N, W) waveform_kernel<N, W><<<grid, 256, 0, s>>>(d_ev, d_theta, n_bins, d_hre, d_him, no_cutoff)
   GWNS_DISPATCH_W(GWNS_WF, 0)
 #undef GWNS_WF
   return cudaGetLastError();

@@ -68,7 +68,7 @@ class ns_progress(C.Structure):
 EXPORTS = ("ns_init", "ns_waveform", "ns_likelihood_batch", "ns_walk_batch", "ns_step", "ns_evidence",
            "ns_posterior", "ns_state_save", "ns_state_load", "ns_walk_batch_noalloc", "ns_flow_num_params",
            "ns_flow_set", "ns_flow_get", "ns_flow_logq", "ns_flow_sample", "ns_flow_grad", "ns_flow_train",
-           "ns_free", "ns_last_error")
+           "ns_relbin_set", "ns_free", "ns_last_error")
 
 _lib = None
 
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
     lib.ns_flow_sample.argtypes = [P, I, C.c_int64, C.c_int64, I, I, P, P, I, V]
     lib.ns_flow_grad.argtypes = [P, I, P, I, P, C.POINTER(C.c_double)]
     lib.ns_flow_train.argtypes = [P, I, P, I, I, P]
+    lib.ns_relbin_set.argtypes = [P, I, P, I, P]
     lib.ns_free.argtypes = [P]
     lib.ns_free.restype = None
     lib.ns_last_error.argtypes = [P]
@@ -324,6 +325,17 @@ def ns_flow_train(h, event: int, u, epochs: int):
     losses = np.zeros(max(epochs, 1))
     _check(_lib.ns_flow_train(h, event, u.ctypes.data, u.shape[0], epochs, losses.ctypes.data), h)
     return losses[:epochs]
+
+
+def ns_relbin_set(h, event: int, edges, theta0=None):
+    """Relative-binning likelihood for the event around the fiducial theta0 [11], coarse-bin
+    edges [n] (grid-bin indices, 0 .. n_bins); edges None restores the full likelihood."""
+    if edges is None:
+        return _check(_lib.ns_relbin_set(h, event, None, 0, None), h)
+    e = np.ascontiguousarray(edges, dtype=np.int32)
+    t = np.ascontiguousarray(theta0, dtype=np.float64)
+    assert t.shape == (11,)
+    return _check(_lib.ns_relbin_set(h, event, e.ctypes.data, e.shape[0], t.ctypes.data), h)
 
 
 def ns_free(h):

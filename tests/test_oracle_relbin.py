@@ -81,3 +81,14 @@ def test_close_to_the_full_likelihood_in_the_posterior_bulk(name):
         got = relbin.log_likelihood(ev, th, sd, w.waveform)
         worst = max(worst, abs(got - want))
     assert worst < 0.05, worst
+
+
+@pytest.mark.parametrize("name", ["four_param_2det_taylorf2", "bbh11_3det_4s_taylorf2", "bbh11_3det_8s_phenomd"])
+def test_library_edges_follow_the_same_rule(name):
+    # The library's host-side edge rule (paper_2509_04336_gb300/relbin.py, written separately)
+    # gives the oracle's edges.
+    from paper_2509_04336_gb300 import relbin as R
+    w = synth.workload(name)
+    for eps in (0.1, 0.25, 1.0, 3.0):
+        assert np.array_equal(R.coarse_edges(w.f_min, w.df, w.n_bins, eps),
+                              relbin.default_edges(w.f_min, w.df, w.n_bins, eps))
