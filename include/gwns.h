@@ -156,6 +156,7 @@ typedef struct ns_progress {
     int32_t n_steps;      /* walk length of the next batch                          */
     int32_t done;         /* termination reached                                    */
     int64_t n_bins;       /* active (walker, bin) pairs evaluated by walks so far    */
+                          /* (relative binning: the edges and exact-range bins)    */
     double walk_ms;       /* device time of this handle's walk launches so far [ms], */
                           /* from CUDA events on the launching stream (all events)  */
     int64_t kernel_launches; /* kernels launched by ns_step so far (all events)     */

@@ -326,9 +326,10 @@ __device__ __forceinline__ void pd_ff_r0_amp(const EventDev& ev, const WalkerPar
 // (every lane returns it).  Coarse bins wholly below the proposal's cutoff whose right edge is
 // a grid bin take the linear expansion of r = h / h0 between their edges (31 bins a pass; lane
 // l holds edge base + l and reads its right neighbour by a shuffle); from the first other coarse
-// bin up to the cutoff the active bins are summed exactly with the per-bin bodies.
+// bin up to the cutoff the active bins are summed exactly with the per-bin bodies.  *bins
+// receives the grid bins the evaluation touched (edges plus the exact range).
 template <int NDET, int WF>
-__device__ double rb_lnl_warp(const EventDev& ev, const WalkerParams& P, int lane) {
+__device__ double rb_lnl_warp(const EventDev& ev, const WalkerParams& P, int lane, int* bins = nullptr) {
   const int nb = ev.rb_nb;
   const int32_t* E = ev.rb_edges;
   const int k_end = P.k_end;
@@ -390,6 +391,7 @@ __device__ double rb_lnl_warp(const EventDev& ev, const WalkerParams& P, int lan
   }
   // exact part: the active bins from the first coarse bin not expanded
   const int kx = E[n_full];
+  if (bins) *bins = n_full + 1 + max(k_end - kx, 0);
   double xdh = 0.0, xhh = 0.0;
   if (WF == 0) {
     AccF32 acc;
@@ -960,6 +962,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   __shared__ int cstep[kSpecMax];
   __shared__ float part_sums[kSpecMax][2 * kMaxVals];
   __shared__ double s_rbl[kSpecMax];   // relative binning: ln L of each proposal
+  __shared__ int s_rbk[kSpecMax];      // and the grid bins it touched
   // IMRPhenomD form: every warp's compensated sums of every proposal
   __shared__ float wsums[WF == 1 ? kSpecMax : 1][kWarps][2 * kMaxVals];
   __shared__ double u[kMaxDim];
@@ -1137,8 +1140,9 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
     if (rb) {
       // relative binning (~10^2 coarse-bin edges a proposal): a warp per proposal
       for (int i = warp; i < nin; i += kWarps) {
-        const double v = rb_lnl_warp<NDET, WF>(ev, P[i], lane);
-        if (lane == 0) s_rbl[i] = v;
+        int nk;
+        const double v = rb_lnl_warp<NDET, WF>(ev, P[i], lane, &nk);
+        if (lane == 0) { s_rbl[i] = v; s_rbk[i] = nk; }
       }
       __syncthreads();
     } else if (WF == 1) {
@@ -1197,7 +1201,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
       const unsigned am = __ballot_sync(0xffffffffu, lane < nin && l > lnl_star);
       const int c = am ? __ffs(am) - 1 : -1;
       const int used = c >= 0 ? c + 1 : nin;
-      int kb = lane < used ? P[lane].k_end : 0;
+      int kb = lane < used ? (rb ? s_rbk[lane] : P[lane].k_end) : 0;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) kb += __shfl_xor_sync(0xffffffffu, kb, off);
       if (c >= 0) {

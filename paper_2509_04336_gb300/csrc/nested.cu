@@ -637,7 +637,7 @@ extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
     // moves time.
     int64_t it_now = h->host_ns.empty() ? 0 : h->host_ns[0].iteration;
     // First cap, from the cost structure once a batch has run: a proposal of fewer than ~1k
-    // active bins is a short likelihood whose rounds are dominated by fixed costs (largest
+    // active bins (with relative binning: edges plus exact-range bins) is a short likelihood whose rounds are dominated by fixed costs (largest
     // cap); a longer one costs a full evaluation per speculative proposal (small cap).
     if (h->tune && !h->tune_guessed && it_now >= 1) {
       double bins = 0.0, evals = 0.0;
