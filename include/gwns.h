@@ -279,6 +279,25 @@ int ns_flow_grad(ns_handle* h, int event, const double* u, int n, float* grad, d
  * -ln q; losses [epochs] (may be NULL) receives the loss before each step. */
 int ns_flow_train(ns_handle* h, int event, const double* u, int n, int epochs, double* losses);
 
+/* ---- hit-and-run slice sampling (the inner kernel named in Sec. 2.2 and Sec. 5; Neal 2003) ----
+ * One batch of the alternative inner kernel on an NS_PREC_FP64 handle, host arrays: n walkers
+ * start at u0 [n][D] (unit cube) with ln L lnl0 [n] and each make n_steps slice-sampling moves
+ * under ln L > lnl_star.  A move draws a line through the walker with direction C z / |z|
+ * (z standard normal; C C^T the sample covariance of the survivors live_u [n_live_pts][D]),
+ * places a bracket one unit of the line wide at random around the walker, steps out by one unit
+ * while the bracket's ends satisfy the constraint (at most 9 steps, split at random between the
+ * sides), then shrinks it around uniform draws until one satisfies the constraint (at most 100
+ * draws, after which the walker stays).  Points outside the cube cost no likelihood call;
+ * periodic coordinates wrap.  Random numbers: Philox4x64-10, key (seed, event), counters
+ * (step, walker_offset + w, iteration, tag), tags 32..34 normals, 40 bracket, 48.. shrinkage.
+ * Outputs: u_out [n][D], lnl_out [n], n_move [n] (moves made), n_like [n] (likelihood calls).
+ * Errors: NS_EINVAL (other precision, bad sizes, a survivor covariance that is not positive
+ * definite: n_live_pts must exceed D), NS_ENONFINITE, NS_ENOMEM, NS_ECUDA. */
+int ns_hrss_batch(ns_handle* h, int event, const double* live_u, int n_live_pts,
+                  const double* u0, const double* lnl0, double lnl_star, int n, int n_steps,
+                  int64_t iteration, int64_t walker_offset, double* u_out, double* lnl_out,
+                  int32_t* n_move, int32_t* n_like);
+
 /* ---- relative binning (Sec. 3.3 and Sec. 5: the likelihood compression for long signals;
  * Zackay, Dai & Venumadhav 2018) ----
  * Switches event `event` of an NS_PREC_MIXED_FF handle to the relative-binning likelihood.

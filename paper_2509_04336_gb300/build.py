@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "libgwns.so")
 SOURCES = ("api.cu", "kernels.cu", "kernels_p0.cu", "kernels_p1.cu", "kernels_p2.cu", "nested.cu", "noalloc.cu",
-           "flow_kernels.cu", "flow_api.cu", "relbin.cu")
+           "flow_kernels.cu", "flow_api.cu", "relbin.cu", "hrss.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

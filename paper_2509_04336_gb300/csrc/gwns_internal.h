@@ -58,6 +58,11 @@ cudaError_t launch_unit_to_theta(const EventDev* d_ev, const double* d_u, int64_
 // no_cutoff: continue the template above its cutoff (the relative-binning fiducial).
 cudaError_t launch_waveform(int waveform, int n_det, const EventDev* d_ev, const double* d_theta, int n, int n_bins,
                             double* d_hre, double* d_him, cudaStream_t s, int no_cutoff = 0);
+// n walkers x n_steps hit-and-run slice-sampling moves (FP64); d_chol [D][D] lower-triangular.
+cudaError_t launch_hrss(int waveform, int n_det, const EventDev* d_ev, const double* d_chol, const double* d_u0,
+                        const double* d_lnl0, double lnl_star, int n, int n_steps, uint64_t iteration,
+                        int64_t walker_offset, uint64_t key0, uint64_t key1, double* d_uo, double* d_lo,
+                        int32_t* d_nm, int32_t* d_nl, cudaStream_t s);
 // Block b walks walker blk_local[b] of task blk_task[b].
 cudaError_t launch_walk(int precision, int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
                         const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s);

@@ -1247,6 +1247,138 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   }
 }
 
+// ---------------------------------------------------------------- hit-and-run slice sampling
+// FP64 (mode 0).  One CTA per walker; thread 0 runs each move's slice logic and the whole CTA
+// evaluates every in-bounds candidate's ln L.  A move (Neal 2003, stepping out and shrinkage,
+// along a random line): direction d = C z / |z| (z standard normal, C the Cholesky factor of
+// the survivors' covariance), bracket [lo, lo + 1] with lo = -U, stepping out by one unit at a
+// time with a budget of kHrssMaxOut - 1 split as J = floor(kHrssMaxOut V) to the left and the
+// rest to the right while the bracket's end is inside the slice, then shrinkage draws until a
+// point inside the slice (at most kHrssMaxShrink; then the walker stays).  A candidate outside
+// the cube costs no likelihood call; periodic coordinates wrap.  Philox blocks (step, walker,
+// iteration, tag): tags 32 + c the normals (Box-Muller on words (0, 1) and (2, 3)), 40 the
+// bracket (U, V), 48 + j / 4 word j % 4 the j-th shrinkage uniform.
+constexpr int kHrssMaxOut = 10;
+constexpr int kHrssMaxShrink = 100;
+
+template <int NDET, int WF>
+__global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restrict__ evp,
+                                                         const double* __restrict__ chol,
+                                                         const double* __restrict__ u0,
+                                                         const double* __restrict__ lnl0, double lnl_star,
+                                                         int n_steps, uint64_t it, int64_t walker_offset,
+                                                         uint64_t key0, uint64_t key1, double* __restrict__ u_out,
+                                                         double* __restrict__ lnl_out, int32_t* __restrict__ n_move,
+                                                         int32_t* __restrict__ n_like) {
+  __shared__ WalkerParams P;
+  __shared__ double red[kWarps][kMaxVals];
+  __shared__ double vals[kMaxVals];
+  __shared__ double x[kMaxDim], dvec[kMaxDim], pt[kMaxDim];
+  __shared__ int s_eval, s_end;
+  const EventDev& ev = *evp;
+  const int D = ev.n_dim;
+  const int j = blockIdx.x;
+  const uint64_t wid = (uint64_t)(walker_offset + j);
+  if ((int)threadIdx.x < D) x[threadIdx.x] = u0[(size_t)j * D + threadIdx.x];
+  double lnl = lnl0[j];
+  int moves = 0, calls = 0;
+  // thread 0's state of the current move: phase 0 steps out left, 1 right, 2 shrinks
+  double lo = 0.0, hi = 0.0, tc = 0.0;
+  int phase = 2, jl = 0, kr = 0, nsh = 0;
+  __syncthreads();
+  for (int t = 0; t < n_steps; ++t) {
+    if (threadIdx.x == 0) {
+      double z[kMaxDim];
+      for (int c = 0; 4 * c < D; ++c) {
+        const Philox4 b = philox4x64((uint64_t)t, wid, it, 32ull + (uint64_t)c, key0, key1);
+        for (int q = 0; q < 2; ++q) {
+          const double r = sqrt(-2.0 * log(rand_open_unit(b.v[2 * q])));
+          double sn, cs;
+          sincospi(2.0 * rand_open_unit(b.v[2 * q + 1]), &sn, &cs);
+          const int i0 = 4 * c + 2 * q;
+          if (i0 < D) z[i0] = r * cs;
+          if (i0 + 1 < D) z[i0 + 1] = r * sn;
+        }
+      }
+      double nz = 0.0;
+      for (int i = 0; i < D; ++i) nz += z[i] * z[i];
+      nz = sqrt(nz);
+      for (int i = 0; i < D; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k <= i; ++k) acc += chol[i * D + k] * z[k];
+        dvec[i] = acc / nz;
+      }
+      const Philox4 b = philox4x64((uint64_t)t, wid, it, 40ull, key0, key1);
+      lo = -rand_open_unit(b.v[0]);
+      hi = lo + 1.0;
+      jl = (int)floor((double)kHrssMaxOut * rand_open_unit(b.v[1]));
+      kr = kHrssMaxOut - 1 - jl;
+      nsh = 0;
+      phase = jl > 0 ? 0 : (kr > 0 ? 1 : 2);
+    }
+    // step-out evaluations <= kHrssMaxOut - 1, shrinkage draws <= kHrssMaxShrink
+    for (int iter = 0; iter < kHrssMaxOut + kHrssMaxShrink; ++iter) {
+      if (threadIdx.x == 0) {
+        if (phase == 0) {
+          tc = lo;
+        } else if (phase == 1) {
+          tc = hi;
+        } else {
+          const Philox4 b = philox4x64((uint64_t)t, wid, it, 48ull + (uint64_t)(nsh >> 2), key0, key1);
+          tc = lo + (hi - lo) * rand_open_unit(b.v[nsh & 3]);
+        }
+        int inb = 1;
+        for (int i = 0; i < D; ++i) {
+          double v = x[i] + tc * dvec[i];
+          if (ev.prior[ev.dim_param[i]].periodic) v -= floor(v);
+          pt[i] = v;
+          if (!(v >= 0.0 && v <= 1.0)) inb = 0;
+        }
+        s_eval = inb;
+        if (inb) setup_from_unit<0, WF>(ev, pt, P);
+      }
+      __syncthreads();
+      const int evaluate = s_eval;
+      if (evaluate) cta_sums<0, NDET, WF>(ev, P, red, vals);
+      if (threadIdx.x == 0) {
+        bool ins = false;
+        double l = 0.0;
+        if (evaluate) {
+          l = lnl_from_vals<0, NDET, WF>(ev, P, vals);
+          ++calls;
+          ins = l > lnl_star;
+        }
+        int end = 0;
+        if (phase == 0) {
+          if (ins) { lo -= 1.0; --jl; }
+          if (!ins || jl == 0) phase = kr > 0 ? 1 : 2;
+        } else if (phase == 1) {
+          if (ins) { hi += 1.0; --kr; }
+          if (!ins || kr == 0) phase = 2;
+        } else if (ins) {
+          for (int i = 0; i < D; ++i) x[i] = pt[i];
+          lnl = l;
+          ++moves;
+          end = 1;
+        } else {
+          if (tc < 0.0) lo = tc;
+          else hi = tc;
+          if (++nsh == kHrssMaxShrink) end = 1;
+        }
+        s_end = end;
+      }
+      __syncthreads();
+      if (s_end) break;
+    }
+  }
+  if ((int)threadIdx.x < D) u_out[(size_t)j * D + threadIdx.x] = x[threadIdx.x];
+  if (threadIdx.x == 0) {
+    lnl_out[j] = lnl;
+    n_move[j] = moves;
+    n_like[j] = calls;
+  }
+}
+
 }  // namespace
 
 // Launchers of one precision P; each kernels_pP.cu instantiates its own.

@@ -68,7 +68,7 @@ class ns_progress(C.Structure):
 EXPORTS = ("ns_init", "ns_waveform", "ns_likelihood_batch", "ns_walk_batch", "ns_step", "ns_evidence",
            "ns_posterior", "ns_state_save", "ns_state_load", "ns_walk_batch_noalloc", "ns_flow_num_params",
            "ns_flow_set", "ns_flow_get", "ns_flow_logq", "ns_flow_sample", "ns_flow_grad", "ns_flow_train",
-           "ns_relbin_set", "ns_free", "ns_last_error")
+           "ns_relbin_set", "ns_hrss_batch", "ns_free", "ns_last_error")
 
 _lib = None
 
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
     lib.ns_flow_grad.argtypes = [P, I, P, I, P, C.POINTER(C.c_double)]
     lib.ns_flow_train.argtypes = [P, I, P, I, I, P]
     lib.ns_relbin_set.argtypes = [P, I, P, I, P]
+    lib.ns_hrss_batch.argtypes = [P, I, P, I, P, P, D, I, I, C.c_int64, C.c_int64, P, P, P, P]
     lib.ns_free.argtypes = [P]
     lib.ns_free.restype = None
     lib.ns_last_error.argtypes = [P]
@@ -336,6 +337,24 @@ def ns_relbin_set(h, event: int, edges, theta0=None):
     t = np.ascontiguousarray(theta0, dtype=np.float64)
     assert t.shape == (11,)
     return _check(_lib.ns_relbin_set(h, event, e.ctypes.data, e.shape[0], t.ctypes.data), h)
+
+
+def ns_hrss_batch(h, event: int, live_u, u0, lnl0, lnl_star: float, n_steps: int, iteration: int = 0,
+                  walker_offset: int = 0):
+    """Hit-and-run slice-sampling moves of host walkers u0 [n][D] against the survivors
+    live_u [m][D]: (u_out, lnl_out, n_move, n_like)."""
+    live_u = np.ascontiguousarray(live_u, dtype=np.float64)
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    lnl0 = np.ascontiguousarray(lnl0, dtype=np.float64)
+    n = u0.shape[0]
+    uo = np.zeros_like(u0)
+    lo = np.zeros(n)
+    nm = np.zeros(n, dtype=np.int32)
+    nl = np.zeros(n, dtype=np.int32)
+    _check(_lib.ns_hrss_batch(h, event, live_u.ctypes.data, live_u.shape[0], u0.ctypes.data, lnl0.ctypes.data,
+                              float(lnl_star), n, n_steps, iteration, walker_offset, uo.ctypes.data,
+                              lo.ctypes.data, nm.ctypes.data, nl.ctypes.data), h)
+    return uo, lo, nm, nl
 
 
 def ns_free(h):
