@@ -23,6 +23,9 @@ re-standardised and trained for flow_epochs full-batch Adam steps on the n_live 
 survivors, which sample the prior above the new L* that the walks target (warm start:
 weights and Adam state persist); the walk then mixes flow steps with probability p_flow
 (oracle.walk).
+With inner="hrss" the walkers instead make hrss_steps hit-and-run slice-sampling moves each
+(oracle.hrss; the inner kernel the paper names in Sec. 2.2 and Sec. 5) against the survivors,
+with the same starts, deletion and evidence; the move count is fixed (no retuning).
 The final live points each receive weight L_i X / n.  The logZ error is the standard
 deviation over replays that draw every shrinkage factor t ~ Beta(n_j, 1).
 Initial live points: u[i, d] from Philox block (i, d // 4, 0, 3), word d % 4.
@@ -36,6 +39,7 @@ from paper_2509_04336_gb300.synth import TERM_DLOGZ, TERM_FRAC_REMAINING
 
 from .philox import philox4x64_vec, mulhi_vec, open_unit_vec
 from .walk import acceptance_walk
+from .hrss import hrss_walk
 from . import flow as flowmod
 
 
@@ -112,7 +116,10 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
                delay: float | None = None, max_iter: int = 100000, n_replay: int = 200,
                initial_u=None, n_steps0: int | None = None, replay_seed: int = 12345,
                p_flow: float = 0.0, flow_every: int = 1, flow_epochs: int = 50, flow_lr: float = 3e-3,
-               flow_hidden: int = 128, flow_layers: int = 8, flow_bf16: bool = False) -> NestedResult:
+               flow_hidden: int = 128, flow_layers: int = 8, flow_bf16: bool = False,
+               inner: str = "de", hrss_steps: int = 0) -> NestedResult:
+    if inner not in ("de", "hrss"):
+        raise ValueError("inner is 'de' or 'hrss'")
     k = num_delete
     if delay is None:
         delay = float(naccept - 1)
@@ -146,9 +153,14 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
         if flow is not None and it % flow_every == 0:
             flowmod.train(flow, u[surv], flow_epochs, adam, flow_bf16)
         starts = surv[start_indices(k, it, n_live - k, key)]
-        new_u, new_lnl, n_acc, n_call, _ = acceptance_walk(
-            loglike, u[starts], lnl[starts], lnl_star, u[surv], n_steps, periodic, key, it,
-            flow=flow, p_flow=p_flow, flow_bf16=flow_bf16)
+        if inner == "hrss":
+            n_steps = hrss_steps
+            new_u, new_lnl, n_acc, n_call = hrss_walk(loglike, u[starts], lnl[starts], lnl_star, u[surv],
+                                                      n_steps, periodic, key, it)
+        else:
+            new_u, new_lnl, n_acc, n_call, _ = acceptance_walk(
+                loglike, u[starts], lnl[starts], lnl_star, u[surv], n_steps, periodic, key, it,
+                flow=flow, p_flow=p_flow, flow_bf16=flow_bf16)
         u[dead] = new_u
         lnl[dead] = new_lnl
         n_like += int(n_call.sum())

@@ -175,3 +175,42 @@ def test_local_moves_keep_the_slice_edges_populated():
     edge = np.mean(np.abs(u[:, 0] - c) > r - 0.02)
     assert abs(edge - 0.2) < 4.0 * math.sqrt(0.2 * 0.8 / n), edge
     assert _ks(u[:, 0], lambda s: np.clip((s - (c - r)) / (2 * r), 0, 1)) > 1e-3
+
+
+@pytest.mark.parametrize("D,mu,sig", [(2, 0.5, 0.05), (4, 0.03, 0.05)])
+def test_sampler_with_hrss_gives_the_gaussian_evidence(D, mu, sig):
+    # The batched sampler with HRSS as its inner kernel: Z of a normalised Gaussian in U[0,1]^D
+    # is prod_d [Phi((1-mu)/sig) - Phi(-mu/sig)] (the second case truncated by a face).
+    from scipy.stats import norm
+    from oracle import nested
+    c = D * math.log(sig * math.sqrt(2 * math.pi))
+    ll = lambda u: -0.5 * float(np.sum(((u - mu) / sig) ** 2)) - c
+    exact = D * math.log(norm.cdf((1 - mu) / sig) - norm.cdf(-mu / sig))
+    r = nested.run_nested(ll, D, 200, 100, 20, 5000, np.zeros(D, bool), (13, D), inner="hrss", hrss_steps=2 * D)
+    assert abs(r.log_z - exact) < 3.5 * r.log_z_err + 0.05, (r.log_z, exact, r.log_z_err)
+    # every batch moved every walker
+    assert all(st[2] == 2 * D for st in r.stats)
+
+
+def test_hrss_insertion_ranks_uniform():
+    # New points from HRSS moves are draws from the constrained prior: their ln L rank among
+    # the survivors is uniform (Fowlie, Handley & Su 2020).
+    from scipy import stats
+    from oracle import nested
+    c = math.log(0.1 * math.sqrt(2 * math.pi)) * 2
+    ll = lambda u: -0.5 * float(np.sum(((u - 0.5) / 0.1) ** 2)) - c
+    n, k, key = 100, 50, (7, 9)
+    u = nested.initial_live_points(n, 2, key)
+    lnl = np.array([ll(x) for x in u])
+    ranks = []
+    for it in range(12):
+        order = np.lexsort((np.arange(n), lnl))
+        dead, surv = order[:k], order[k:]
+        starts = surv[nested.start_indices(k, it, n - k, key)]
+        new_u, new_lnl, _, _ = hrss.hrss_walk(ll, u[starts], lnl[starts], lnl[dead[-1]], u[surv], 6,
+                                              np.zeros(2, bool), key, it)
+        if it >= 2:
+            sl = np.sort(lnl[surv])
+            ranks.extend(np.searchsorted(sl, new_lnl) / (n - k))
+        u[dead], lnl[dead] = new_u, new_lnl
+    assert stats.kstest(np.array(ranks), "uniform").pvalue > 1e-3
