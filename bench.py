@@ -565,7 +565,10 @@ def run_relbin(args):
                 evals = p[0]["n_like"] - p0[0]["n_like"]
                 arms[tag] = {"lnl_evals_per_s": evals / (ms * 1e-3), "ms_per_step": ms / args.steps,
                              "walk_ms_per_step": (p[0]["walk_ms"] - p0[0]["walk_ms"]) / args.steps,
-                             "spec_depth": p[0]["spec_depth"], "mean_walk_steps": p[0]["n_steps"]}
+                             "spec_depth": p[0]["spec_depth"], "mean_walk_steps": p[0]["n_steps"],
+                             # grid bins an evaluation touched: active bins (full), or edges plus
+                             # the exact range (relative binning)
+                             "bins_per_eval": (p[0]["n_bins"] - p0[0]["n_bins"]) / max(evals, 1)}
             finally:
                 gwns.ns_free(h)
     for tag, ed in (("full", None), ("relbin", edges)):
