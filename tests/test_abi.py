@@ -105,4 +105,6 @@ def test_null_handle_calls_fail_cleanly(lib):
     n = C.c_int32()
     assert lib.ns_flow_num_params(None, 0, C.byref(n)) == gwns.NS_EINVAL
     assert lib.ns_flow_logq(None, 0, None, 0, None, 0, None) == gwns.NS_EINVAL
+    assert lib.ns_relbin_set(None, 0, None, 0, None) == gwns.NS_EINVAL
+    assert lib.ns_hrss_batch(None, 0, None, 0, None, None, 0.0, 0, 0, 0, 0, None, None, None, None) == gwns.NS_EINVAL
     lib.ns_free(None)
