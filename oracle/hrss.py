@@ -69,10 +69,11 @@ def shrink_draw(t: int, walker: int, it: int, j: int, key) -> float:
     return float(open_unit_vec(blk[j % 4])[0])
 
 
-def slice_step(loglike, x, lnl_star, d, periodic, u, v, shrink_uniforms, width=1.0, max_out=10):
+def slice_step(loglike, x, lnl_star, d, periodic, u, v, shrink_uniforms, width=1.0, max_out=10, margins=None):
     """One slice-sampling move of x along d.  shrink_uniforms: iterable of U(0, 1) draws.
     Returns (new x, its ln L or None if the walker stayed, likelihood calls, (lo, hi) of the
-    final bracket, t of the move or None)."""
+    final bracket, t of the move or None).  margins (a list, optional) receives |ln L - ln L*|
+    of every evaluated point: how far each decision was from its threshold."""
     x = np.asarray(x, dtype=np.float64)
     periodic = np.asarray(periodic, dtype=bool)
     calls = 0
@@ -89,6 +90,8 @@ def slice_step(loglike, x, lnl_star, d, periodic, u, v, shrink_uniforms, width=1
             return False, None
         calls += 1
         lnl = loglike(p)
+        if margins is not None:
+            margins.append(abs(lnl - lnl_star))
         return lnl > lnl_star, lnl
 
     lo = -width * u
@@ -114,9 +117,11 @@ def slice_step(loglike, x, lnl_star, d, periodic, u, v, shrink_uniforms, width=1
 
 
 def hrss_walk(loglike, u0, lnl0, lnl_star, survivors, n_steps, periodic, key, it, walker_ids=None,
-              width=1.0, max_out=10, max_shrink=100):
+              width=1.0, max_out=10, max_shrink=100, return_margin=False):
     """n_steps HRSS moves for every walker (rows of u0).  Returns (u, ln L, moves made,
-    likelihood calls) per walker."""
+    likelihood calls) per walker, and with return_margin the smallest |ln L - ln L*| of each
+    walker's decisions (a walker whose margin is below another implementation's ln L error
+    may legitimately take the other branch)."""
     u = np.array(u0, dtype=np.float64, copy=True)
     lnl = np.array(lnl0, dtype=np.float64, copy=True)
     W, D = u.shape
@@ -124,16 +129,22 @@ def hrss_walk(loglike, u0, lnl0, lnl_star, survivors, n_steps, periodic, key, it
     C = direction_factor(survivors)
     n_move = np.zeros(W, dtype=np.int64)
     n_like = np.zeros(W, dtype=np.int64)
+    margin = np.full(W, np.inf)
     for w in range(W):
         wid = int(ids[w])
+        ms = []
         for t in range(n_steps):
             z = step_normals(t, wid, it, D, key)
             d = C @ z / np.linalg.norm(z)
             uu, vv = bracket_draws(t, wid, it, key)
             draws = (shrink_draw(t, wid, it, j, key) for j in range(max_shrink))
-            x, l, calls, _, tm = slice_step(loglike, u[w], lnl_star, d, periodic, uu, vv, draws, width, max_out)
+            x, l, calls, _, tm = slice_step(loglike, u[w], lnl_star, d, periodic, uu, vv, draws, width, max_out, ms)
             n_like[w] += calls
             if tm is not None:
                 u[w], lnl[w] = x, l
                 n_move[w] += 1
+        if ms:
+            margin[w] = min(ms)
+    if return_margin:
+        return u, lnl, n_move, n_like, margin
     return u, lnl, n_move, n_like

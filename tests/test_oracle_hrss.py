@@ -214,3 +214,20 @@ def test_hrss_insertion_ranks_uniform():
             ranks.extend(np.searchsorted(sl, new_lnl) / (n - k))
         u[dead], lnl[dead] = new_u, new_lnl
     assert stats.kstest(np.array(ranks), "uniform").pvalue > 1e-3
+
+
+def test_margin_is_the_closest_decision():
+    # The margin is the smallest |ln L - ln L*| over every evaluated candidate; it never exceeds
+    # the distance of the accepted end point from the threshold.
+    c = 0.5
+    like = lambda p: -float(np.sum((p - c) ** 2))
+    rng = np.random.default_rng(12)
+    x0 = c + 0.1 * (rng.random((20, 2)) - 0.5)
+    l0 = [like(p) for p in x0]
+    star = -0.01
+    u, l, moved, calls, margin = hrss.hrss_walk(like, x0, l0, star, x0, 2, [False, False], KEY, 0,
+                                                return_margin=True)
+    assert np.all(margin <= np.abs(l - star) + 1e-15)
+    assert np.all(margin > 0.0) and np.all(np.isfinite(margin))
+    u2, l2, m2, c2 = hrss.hrss_walk(like, x0, l0, star, x0, 2, [False, False], KEY, 0)
+    assert np.array_equal(u, u2) and np.array_equal(calls, c2)
