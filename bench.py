@@ -196,6 +196,26 @@ def oracle_walk_rate(w: synth.Workload, ev: synth.Event, budget_s: float, walker
                                    f"{w.n_bins} bins x {len(w.detectors)} detectors"}
 
 
+def oracle_relbin_rate(w: synth.Workload, ev: synth.Event, edges, budget_s: float, max_evals: int | None = None):
+    """ln L evals/s of the oracle's relative-binning likelihood (single thread) on prior draws,
+    after its summary data (not timed) around the injection."""
+    from oracle import prior as P, relbin as RB
+
+    pri = synth.priors_with_injection(w, ev)
+    sd = RB.summary_data(ev, ev.theta_inj, edges, w.waveform)
+    pts = synth.uniform_unit_cube(256, w.n_dim, 98)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        RB.log_likelihood(ev, P.transform(pts[n % 256], pri), sd, w.waveform, w.use_ratio)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_evals is not None and n >= max_evals):
+            break
+    return n / el, {"evals": n, "seconds": el,
+                    "sample": f"{n} relative-binning ln L evaluations at prior draws, {len(edges) - 1} coarse bins, "
+                              f"{w.n_bins} bins x {len(w.detectors)} detectors"}
+
+
 def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
@@ -564,6 +584,8 @@ def run_relbin(args):
                     ms += e0.elapsed_time(e1)
                 evals = p[0]["n_like"] - p0[0]["n_like"]
                 arms[tag] = {"lnl_evals_per_s": evals / (ms * 1e-3), "ms_per_step": ms / args.steps,
+                             "_bins": p[0]["n_bins"] - p0[0]["n_bins"], "_spec": p[0]["n_spec"] - p0[0]["n_spec"],
+                             "_evals": evals, "_walk_ms": p[0]["walk_ms"] - p0[0]["walk_ms"],
                              "walk_ms_per_step": (p[0]["walk_ms"] - p0[0]["walk_ms"]) / args.steps,
                              "spec_depth": p[0]["spec_depth"], "mean_walk_steps": p[0]["n_steps"],
                              # grid bins an evaluation touched: active bins (full), or edges plus
@@ -574,6 +596,16 @@ def run_relbin(args):
     for tag, ed in (("full", None), ("relbin", edges)):
         arms[tag]["to_logz"] = run_to_logz(gwns, w, ev, synth.PREC_MIXED_FF, local, relbin_edges=ed)
     ck = clocks.summary()
+    # roofline of the walk on the relative-binning path: the per-bin FP32 count of the waveform
+    # for every grid bin an evaluation touched (edges and exact range), speculative ones included
+    rb = arms["relbin"]
+    flops_bin = FP32_FLOPS_PER_WALKER_BIN if w.waveform == synth.TAYLORF2 else FP32_FLOPS_PER_WALKER_BIN_PD
+    touched = rb["_bins"] * rb["_spec"] / max(rb["_evals"], 1)
+    achieved = touched * flops_bin / (rb["_walk_ms"] * 1e-3) / 1e12
+    for a in arms.values():
+        for key in ("_bins", "_spec", "_evals", "_walk_ms"):
+            a.pop(key)
+    cpu_rate, cpu_info = oracle_relbin_rate(w, ev, edges, args.cpu_seconds)
     line = {
         "metric": "relative-binning likelihood: lnL evals/s and wall time to ln Z against the full likelihood",
         "value": arms["relbin"]["lnl_evals_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -586,6 +618,13 @@ def run_relbin(args):
         "speedup_evals": arms["relbin"]["lnl_evals_per_s"] / arms["full"]["lnl_evals_per_s"],
         "speedup_to_logz": arms["full"]["to_logz"]["seconds"] / arms["relbin"]["to_logz"]["seconds"],
         "abs_delta_log_z": abs(arms["full"]["to_logz"]["log_z"] - arms["relbin"]["to_logz"]["log_z"]),
+        "roofline": {"bound": "alu", "pipe": "fp32",
+                     "kernel": f"walk_kernel_ff<3,{w.waveform}> (relative-binning path)",
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "counted": "FP32 flops of the per-bin body for every grid bin touched (edges, exact "
+                                "range); the per-proposal constants are not counted"},
+        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_info["sample"]},
         "clocks": {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons", [])},
     }
     print(json.dumps(line))
