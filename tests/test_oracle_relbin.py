@@ -92,3 +92,29 @@ def test_library_edges_follow_the_same_rule(name):
     for eps in (0.1, 0.25, 1.0, 3.0):
         assert np.array_equal(R.coarse_edges(w.f_min, w.df, w.n_bins, eps),
                               relbin.default_edges(w.f_min, w.df, w.n_bins, eps))
+
+
+@pytest.mark.parametrize("name", ["bbh11_3det_4s_taylorf2", "bbh11_3det_8s_phenomd"])
+def test_summary_data_are_exact_for_a_linear_ratio(name):
+    # For any ratio linear in f, r(f) = alpha + beta f (complex), the summary data reproduce
+    # <d|h0 r> and <h0 r|h0 r> exactly: sum_b Re(A0 r_b + A1 beta) and
+    # sum_b B0 |r_b|^2 + 2 B1 Re(conj(r_b) beta) + B2 |beta|^2, with r_b = r(f at edge b).
+    # Every summary coefficient enters (a dropped term, a sign or a wrong offset fails).
+    from paper_2509_04336_gb300.synth import frequencies
+    w, ev = event(name)
+    edges = relbin.default_edges(ev.f_min, ev.df, ev.n_bins, eps=1.0)
+    sd = relbin.summary_data(ev, ev.theta_inj, edges, w.waveform)
+    f = frequencies(ev.f_min, ev.df, ev.n_bins)
+    alpha, beta = 0.7 - 0.4j, (2.0 + 1.5j) / (f[-1] - f[0])
+    r_f = alpha + beta * f
+    r_e = alpha + beta * sd["fe"][:-1]
+    for i, d in enumerate(ev.detectors):
+        h0 = L.project(ev, i, ev.theta_inj, w.waveform, cutoff=False)
+        wgt = 4.0 * ev.df / d.psd
+        dh_direct = float(np.sum((np.conj(d.data) * h0 * r_f).real * wgt))
+        hh_direct = float(np.sum(np.abs(h0 * r_f) ** 2 * wgt))
+        dh_sd = float(np.sum((sd["A0"][i] * r_e + sd["A1"][i] * beta).real))
+        hh_sd = float(np.sum(sd["B0"][i] * np.abs(r_e) ** 2 + 2.0 * sd["B1"][i] * (np.conj(r_e) * beta).real
+                             + sd["B2"][i] * abs(beta) ** 2))
+        assert abs(dh_sd - dh_direct) <= 1e-9 * max(abs(dh_direct), hh_direct)
+        assert abs(hh_sd - hh_direct) <= 1e-9 * hh_direct
