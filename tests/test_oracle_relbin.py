@@ -118,3 +118,22 @@ def test_summary_data_are_exact_for_a_linear_ratio(name):
                              + sd["B2"][i] * abs(beta) ** 2))
         assert abs(dh_sd - dh_direct) <= 1e-9 * max(abs(dh_direct), hh_direct)
         assert abs(hh_sd - hh_direct) <= 1e-9 * hh_direct
+
+
+@pytest.mark.parametrize("name", ["bbh11_3det_4s_taylorf2", "bbh11_3det_8s_phenomd"])
+def test_coarse_bin_holding_the_cutoff_is_summed_exactly(name):
+    # One grid bin per coarse bin except a wide one around the proposal's cutoff: the narrow
+    # bins are exact, the wide one is the exact range (summed bin by bin up to the cutoff) and
+    # the bins above contribute nothing, so the compressed ln L is the full one.
+    w, ev = event(name)
+    th = ev.theta_inj.copy()
+    k_end = relbin.active_bins(ev, th, w.waveform)
+    assert 40 < k_end < ev.n_bins - 40
+    lo, hi = k_end - 20, k_end + 30
+    edges = np.concatenate([np.arange(0, lo + 1), np.arange(hi, ev.n_bins + 1)])
+    sd = relbin.summary_data(ev, ev.theta_inj, edges, w.waveform)
+    assert relbin.n_expanded(edges, k_end, ev.n_bins) == lo
+    for t in (th, th + np.array([0, 0, 0, 0, 30.0, 0.1, 0.1, 0.2, 1e-4, 0.01, 0.01])):
+        assert relbin.active_bins(ev, t, w.waveform) == k_end
+        want = L.log_likelihood(ev, t, w.waveform)
+        assert abs(relbin.log_likelihood(ev, t, sd, w.waveform) - want) <= 1e-9 * abs(want)
