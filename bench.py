@@ -550,7 +550,7 @@ def run_relbin(args):
     from ns_init to its stopping rule (wall time to ln Z and the evidence)."""
     import torch
 
-    from paper_2509_04336_gb300 import build, gwns, relbin
+    from paper_2509_04336_gb300 import build, gwns
 
     rank, world, local = rank_info()
     if rank != 0:
@@ -559,7 +559,7 @@ def run_relbin(args):
     build.build()
     gwns.load()
     w, ev = library_event(synth.workload(args.workload), 0, local)
-    edges = relbin.coarse_edges(ev.f_min, ev.df, ev.n_bins, args.relbin)
+    edges = gwns.ns_relbin_edges(ev.f_min, ev.df, ev.n_bins, args.relbin)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     arms = {}
     with ClockSampler(local) as clocks:

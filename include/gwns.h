@@ -29,7 +29,9 @@
  *     memory.  Caller buffers are borrowed for the duration of the call only; with
  *     device pointers the work is enqueued on `stream` and the call returns after
  *     enqueueing (the caller synchronises); with host pointers the call blocks.
- *   - stream == NULL means the handle's own stream.
+ *   - stream == NULL means the handle's own stream (created non-blocking, so it is not ordered
+ *     with the legacy default stream); to order a call with work on the legacy default stream
+ *     pass cudaStreamLegacy.
  *   - The library owns every buffer it allocates; ns_free releases them.
  *   - One handle per host thread; a handle is bound to the device given to ns_init.
  */
@@ -209,7 +211,11 @@ int ns_walk_batch(ns_handle* h, int event, const double* live_u, int n_live_pts,
  * enqueued on `stream` and the call returns without waiting.  At most 8192 walkers per
  * call (NS_EINVAL beyond).  The first call on a device looks up the array's address; make
  * it before any stream capture.  Calls whose kernels overlap on the GPU share the array and
- * race: order them on one stream.  Results equal ns_walk_batch's for the same arguments. */
+ * race: order them on one stream.  Results equal ns_walk_batch's for the same arguments.
+ * An event with flow proposals (NS_PROPOSAL_DE_FLOW, p_flow > 0) writes its proposal table
+ * into the handle's own batch table, which ns_step also uses: there n <= num_delete and
+ * n_steps <= maxmcmc (NS_EINVAL beyond), and the call must not overlap an ns_step of the
+ * same handle on the GPU. */
 int ns_walk_batch_noalloc(ns_handle* h, int event, const double* live_u, int n_live_pts,
                           const double* u0, const double* lnl0, double lnl_star,
                           int n, int n_steps, int64_t iteration, int64_t walker_offset,
@@ -316,6 +322,17 @@ int ns_hrss_batch(ns_handle* h, int event, const double* live_u, int n_live_pts,
  * Errors: NS_EINVAL (other precision, bad edges, after the first step, a fiducial that vanishes
  * at an edge), NS_ENONFINITE (theta0 or the summary data), NS_ENOMEM, NS_ECUDA. */
 int ns_relbin_set(ns_handle* h, int event, const int32_t* edges, int n_edges, const double* theta0);
+
+/* Coarse-bin edges for ns_relbin_set on the grid f_k = f_min + k df, k < n_bins (the bin-width
+ * rule of Zackay, Dai & Venumadhav 2018, which the paper's Sec. 3.3 and Sec. 5 name): with
+ * dpsi(f) = 2 pi sum_g sign(g) (f / f_g)^g over g = -5/3, -2/3, 1, 5/3, 7/3 (f_g = f_min for
+ * g < 0, the top bin's frequency for g > 0), a bound on how far any template's phase can drift
+ * from the fiducial's, each edge after 0 is the first grid bin whose dpsi differs from the
+ * previous edge's by more than eps radians; the last edge is n_bins.  Host arithmetic only, no
+ * handle and no device: edges [cap] (host, caller-owned) receives min(cap, *n_edges) edges.
+ * Returns NS_EINVAL for f_min, df or eps not positive and finite, n_bins < 1, a null n_edges,
+ * or cap < *n_edges (then *n_edges still holds the count needed). */
+int ns_relbin_edges(double f_min, double df, int n_bins, double eps, int32_t* edges, int cap, int32_t* n_edges);
 
 void ns_free(ns_handle* h);
 const char* ns_last_error(ns_handle* h);

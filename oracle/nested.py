@@ -29,6 +29,9 @@ with the same starts, deletion and evidence; the move count is fixed (no retunin
 The final live points each receive weight L_i X / n.  The logZ error is the standard
 deviation over replays that draw every shrinkage factor t ~ Beta(n_j, 1).
 Initial live points: u[i, d] from Philox block (i, d // 4, 0, 3), word d % 4.
+A process pool (walk_pool) only spreads the DE walks of a batch over processes, in
+contiguous walker ranges with their own walker ids; a walker's chain depends on its id
+alone, so the result is the same as the one-process run's.
 """
 import math
 from dataclasses import dataclass, field
@@ -111,13 +114,24 @@ def log_z_replays(dead_lnl, dead_nlive, live_lnl, n_replay: int, rng) -> np.ndar
     return out
 
 
+def _pooled_walk(pool, n_chunks, loglike, u0, lnl0, lnl_star, survivors, n_steps, periodic, key, it):
+    """acceptance_walk over walker ranges in a process pool (same chains, same order)."""
+    k = u0.shape[0]
+    edges = np.linspace(0, k, max(1, n_chunks) + 1).astype(int)
+    args = [(loglike, u0[a:b], lnl0[a:b], lnl_star, survivors, n_steps, periodic, key, it, np.arange(a, b))
+            for a, b in zip(edges[:-1], edges[1:]) if b > a]
+    parts = pool.starmap(acceptance_walk, args, chunksize=1)
+    return tuple(np.concatenate([p[i] for p in parts]) for i in range(5))
+
+
 def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, maxmcmc: int,
                periodic, key, term_kind: int = TERM_DLOGZ, term_value: float = 0.1,
                delay: float | None = None, max_iter: int = 100000, n_replay: int = 200,
                initial_u=None, n_steps0: int | None = None, replay_seed: int = 12345,
                p_flow: float = 0.0, flow_every: int = 1, flow_epochs: int = 50, flow_lr: float = 3e-3,
                flow_hidden: int = 128, flow_layers: int = 8, flow_bf16: bool = False,
-               inner: str = "de", hrss_steps: int = 0) -> NestedResult:
+               inner: str = "de", hrss_steps: int = 0, walk_pool=None, walk_chunks: int = 1,
+               progress=None) -> NestedResult:
     if inner not in ("de", "hrss"):
         raise ValueError("inner is 'de' or 'hrss'")
     k = num_delete
@@ -157,6 +171,10 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
             n_steps = hrss_steps
             new_u, new_lnl, n_acc, n_call = hrss_walk(loglike, u[starts], lnl[starts], lnl_star, u[surv],
                                                       n_steps, periodic, key, it)
+        elif walk_pool is not None and flow is None:
+            new_u, new_lnl, n_acc, n_call, _ = _pooled_walk(
+                walk_pool, walk_chunks, loglike, u[starts], lnl[starts], lnl_star, u[surv], n_steps,
+                periodic, key, it)
         else:
             new_u, new_lnl, n_acc, n_call, _ = acceptance_walk(
                 loglike, u[starts], lnl[starts], lnl_star, u[surv], n_steps, periodic, key, it,
@@ -166,6 +184,8 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
         n_like += int(n_call.sum())
         mean_acc = float(n_acc.mean())
         stats.append((it, n_steps, mean_acc, int(n_call.sum()), lnl_star, log_z))
+        if progress is not None:
+            progress(stats[-1])
         n_steps = retune(n_steps, mean_acc, naccept, delay_k, maxmcmc)
         it += 1
         if term_kind == TERM_DLOGZ:

@@ -18,6 +18,9 @@
 //    streams, or different handles on the same device) race on it: order them on one stream.
 //  * All array arguments are device pointers; the work is enqueued on `stream` (NULL: the
 //    handle's stream) and the call returns without waiting for it.
+//  * An event with flow proposals (NS_PROPOSAL_DE_FLOW, p_flow > 0) writes its proposal table
+//    into the handle's own batch table, which ns_step also uses: then n <= num_delete and
+//    n_steps <= maxmcmc, and a call must not overlap an ns_step of the same handle.
 #include <cstring>
 #include <mutex>
 
@@ -106,6 +109,8 @@ extern "C" int ns_walk_batch_noalloc(ns_handle* h, int event, const double* live
   T.event = event;
   T.spec = E.cfg.spec_depth > 0 ? E.cfg.spec_depth : default_spec(h->precision);
   cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+  // the flow kernels' timeout flag starts clear, as in ns_walk_batch
+  if ((e = cudaMemsetAsync(h->d_status + 1, 0, sizeof(int32_t), s)) != cudaSuccess) return cuda_fail(h, e, "status reset");
   // flow steps draw on the handle's own proposal table, allocated at ns_init
   r = flow_attach(h, event, T, n, n_steps, nullptr, s);
   if (r) return r;

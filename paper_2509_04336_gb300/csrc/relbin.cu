@@ -37,13 +37,22 @@ void relbin_free(EventHost& E) {
   E.dev.rb_b = nullptr;
 }
 
-// Publishes E.dev to the device copy and re-evaluates the initial live points with the
-// likelihood now in effect.
-static int relbin_publish(ns_handle* h, int event) {
+// Makes `nd` the event's descriptor: uploads it to the device copy first (a synchronous copy;
+// until it succeeds the old descriptor and its arrays stay in place and valid), then adopts
+// the new relative-binning arrays, frees the old ones (cudaFree waits for kernels still
+// reading them) and re-evaluates the initial live points with the likelihood now in effect.
+// On an upload failure the caller still owns the new arrays.
+static int relbin_adopt(ns_handle* h, int event, const EventDev& nd, int32_t* ed, float2* q0, float2* a, float4* b) {
   EventHost& E = h->events[event];
   cudaError_t e;
-  if ((e = cudaMemcpy(h->d_events + event, &E.dev, sizeof(EventDev), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = cudaMemcpy(h->d_events + event, &nd, sizeof(EventDev), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(h, e, "event upload");
+  relbin_free(E);
+  E.dev = nd;
+  E.d_rb_edges = ed;
+  E.d_rb_q0 = q0;
+  E.d_rb_a = a;
+  E.d_rb_b = b;
   NsState& S = E.ns;
   if (S.live_u && S.live_lnl && S.n_live > 0) {
     if ((e = launch_unit_likelihood(h->precision, h->waveform, E.n_det, h->d_events + event, S.live_u, S.n_live,
@@ -52,6 +61,48 @@ static int relbin_publish(ns_handle* h, int event) {
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "initial likelihoods");
   }
   return NS_OK;
+}
+
+// The coarse-bin edge rule (Zackay, Dai & Venumadhav 2018): a coarse bin ends where the largest
+// phase difference a template can have from the fiducial could have changed by eps radians.
+// That difference is bounded by a sum of the phase's power laws f^g (g = -5/3, -2/3, 1, 5/3,
+// 7/3), each normalised at the end of the band where it is largest:
+// dpsi(f) = 2 pi sum_g sign(g) (f / f_g)^g, f_g = f_min for g < 0 and the band's top for g > 0.
+// Each edge is the first grid bin whose dpsi differs from the previous edge's by more than eps
+// (a coarse bin holds at least one grid bin).
+extern "C" int ns_relbin_edges(double f_min, double df, int n_bins, double eps, int32_t* edges, int cap,
+                               int32_t* n_edges) {
+  if (!(f_min > 0.0) || !(df > 0.0) || n_bins < 1 || !(eps > 0.0) || !std::isfinite(f_min + df + eps) || !n_edges ||
+      cap < 0 || (cap > 0 && !edges))
+    return NS_EINVAL;
+  static const double g[5] = {-5.0 / 3.0, -2.0 / 3.0, 1.0, 5.0 / 3.0, 7.0 / 3.0};
+  const double f_top = f_min + df * (double)(n_bins - 1);
+  std::vector<double> dpsi(n_bins);
+  for (int k = 0; k < n_bins; ++k) {
+    const double f = f_min + df * (double)k;
+    double s = 0.0;
+    for (int i = 0; i < 5; ++i) {
+      const double ref = g[i] < 0.0 ? f_min : f_top;
+      s += (g[i] < 0.0 ? -1.0 : 1.0) * 2.0 * M_PI * std::pow(f / ref, g[i]);
+    }
+    dpsi[k] = s;
+  }
+  int32_t count = 0;
+  auto put = [&](int32_t v) {
+    if (count < cap) edges[count] = v;
+    ++count;
+  };
+  int last = 0;
+  put(0);
+  for (int k = 1; k < n_bins; ++k) {
+    if (std::fabs(dpsi[k] - dpsi[last]) > eps) {
+      put(k);
+      last = k;
+    }
+  }
+  put(n_bins);
+  *n_edges = count;
+  return count <= cap ? NS_OK : NS_EINVAL;
 }
 
 extern "C" int ns_relbin_set(ns_handle* h, int event, const int32_t* edges, int n_edges, const double* theta0) {
@@ -77,8 +128,13 @@ extern "C" int ns_relbin_set(ns_handle* h, int event, const int32_t* edges, int 
   cudaSetDevice(h->device);
   cudaGetLastError();
   if (n_edges == 0) {
-    relbin_free(E);
-    return relbin_publish(h, event);
+    EventDev nd = E.dev;
+    nd.rb_nb = 0;
+    nd.rb_edges = nullptr;
+    nd.rb_q0 = nullptr;
+    nd.rb_a = nullptr;
+    nd.rb_b = nullptr;
+    return relbin_adopt(h, event, nd, nullptr, nullptr, nullptr, nullptr);
   }
   const int nb = n_edges - 1;
   // the fiducial, continued above its cutoff, and the event's weighted data
@@ -143,25 +199,37 @@ extern "C" int ns_relbin_set(ns_handle* h, int event, const int32_t* edges, int 
         return set_error(h, NS_ENONFINITE, "summary data not finite (coarse bin %d, detector %d)", c, d);
     }
   }
-  relbin_free(E);
-  if ((e = cudaMalloc(&E.d_rb_edges, sizeof(int32_t) * (nb + 1))) != cudaSuccess ||
-      (e = cudaMalloc(&E.d_rb_q0, sizeof(float2) * q0.size())) != cudaSuccess ||
-      (e = cudaMalloc(&E.d_rb_a, sizeof(float2) * a.size())) != cudaSuccess ||
-      (e = cudaMalloc(&E.d_rb_b, sizeof(float4) * b.size())) != cudaSuccess) {
-    relbin_free(E);
+  // new arrays first; the event keeps its current ones until the new descriptor is on the device
+  int32_t* ned = nullptr;
+  float2 *nq0 = nullptr, *na = nullptr;
+  float4* nbb = nullptr;
+  auto drop = [&]() {
+    cudaFree(ned);
+    cudaFree(nq0);
+    cudaFree(na);
+    cudaFree(nbb);
+  };
+  if ((e = cudaMalloc(&ned, sizeof(int32_t) * (nb + 1))) != cudaSuccess ||
+      (e = cudaMalloc(&nq0, sizeof(float2) * q0.size())) != cudaSuccess ||
+      (e = cudaMalloc(&na, sizeof(float2) * a.size())) != cudaSuccess ||
+      (e = cudaMalloc(&nbb, sizeof(float4) * b.size())) != cudaSuccess) {
+    drop();
     return set_error(h, NS_ENOMEM, "relative-binning allocation failed: %s", cudaGetErrorString(e));
   }
-  if ((e = cudaMemcpy(E.d_rb_edges, edges, sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(E.d_rb_q0, q0.data(), sizeof(float2) * q0.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(E.d_rb_a, a.data(), sizeof(float2) * a.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(E.d_rb_b, b.data(), sizeof(float4) * b.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
-    relbin_free(E);
+  if ((e = cudaMemcpy(ned, edges, sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(nq0, q0.data(), sizeof(float2) * q0.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(na, a.data(), sizeof(float2) * a.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(nbb, b.data(), sizeof(float4) * b.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    drop();
     return cuda_fail(h, e, "relative-binning upload");
   }
-  E.dev.rb_nb = nb;
-  E.dev.rb_edges = E.d_rb_edges;
-  E.dev.rb_q0 = E.d_rb_q0;
-  E.dev.rb_a = E.d_rb_a;
-  E.dev.rb_b = E.d_rb_b;
-  return relbin_publish(h, event);
+  EventDev ndev = E.dev;
+  ndev.rb_nb = nb;
+  ndev.rb_edges = ned;
+  ndev.rb_q0 = nq0;
+  ndev.rb_a = na;
+  ndev.rb_b = nbb;
+  r = relbin_adopt(h, event, ndev, ned, nq0, na, nbb);
+  if (r && E.d_rb_edges != ned) drop();   // the descriptor upload failed: the old state stands
+  return r;
 }

@@ -1,7 +1,8 @@
 """Python binding of libgwns (include/gwns.h): argument marshalling only.
 
 Every function has the name and argument order of its C counterpart.  Arrays may be
-torch tensors (CUDA tensors are passed as device pointers on the current torch stream,
+torch tensors (CUDA tensors are passed as device pointers on the current torch stream --
+torch's default stream as cudaStreamLegacy, so the library's work is ordered with torch's --
 CPU tensors as host pointers) or numpy arrays (host pointers).  Loading fails loudly when
 the shared library has not been built: there is no fallback path.
 """
@@ -68,7 +69,7 @@ class ns_progress(C.Structure):
 EXPORTS = ("ns_init", "ns_waveform", "ns_likelihood_batch", "ns_walk_batch", "ns_step", "ns_evidence",
            "ns_posterior", "ns_state_save", "ns_state_load", "ns_walk_batch_noalloc", "ns_flow_num_params",
            "ns_flow_set", "ns_flow_get", "ns_flow_logq", "ns_flow_sample", "ns_flow_grad", "ns_flow_train",
-           "ns_relbin_set", "ns_hrss_batch", "ns_free", "ns_last_error")
+           "ns_relbin_set", "ns_relbin_edges", "ns_hrss_batch", "ns_free", "ns_last_error")
 
 _lib = None
 
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH):
     lib.ns_flow_grad.argtypes = [P, I, P, I, P, C.POINTER(C.c_double)]
     lib.ns_flow_train.argtypes = [P, I, P, I, I, P]
     lib.ns_relbin_set.argtypes = [P, I, P, I, P]
+    lib.ns_relbin_edges.argtypes = [D, D, I, D, P, I, C.POINTER(C.c_int32)]
     lib.ns_hrss_batch.argtypes = [P, I, P, I, P, P, D, I, I, C.c_int64, C.c_int64, P, P, P, P]
     lib.ns_free.argtypes = [P]
     lib.ns_free.restype = None
@@ -135,8 +137,21 @@ def _ptr(a):
     if not a.is_contiguous():
         raise ValueError("tensors must be contiguous")
     if a.is_cuda:
-        return a.data_ptr(), NS_PTR_DEVICE, torch.cuda.current_stream(a.device).cuda_stream
+        return a.data_ptr(), NS_PTR_DEVICE, _torch_stream(a.device)
     return a.data_ptr(), NS_PTR_HOST, None
+
+
+# cudaStreamLegacy: the handle value that names the legacy default stream explicitly.
+CUDA_STREAM_LEGACY = 0x1
+
+
+def _torch_stream(device):
+    """Stream handle of torch's current stream on `device`, never NULL: torch's default stream
+    is the legacy default stream (handle 0), and a NULL stream means the handle's own stream to
+    the library, which is not ordered with torch's work; it is passed as cudaStreamLegacy."""
+    import torch
+    st = torch.cuda.current_stream(device).cuda_stream
+    return st if st != 0 else CUDA_STREAM_LEGACY
 
 
 def _same_kind(*arrays):
@@ -337,6 +352,18 @@ def ns_relbin_set(h, event: int, edges, theta0=None):
     t = np.ascontiguousarray(theta0, dtype=np.float64)
     assert t.shape == (11,)
     return _check(_lib.ns_relbin_set(h, event, e.ctypes.data, e.shape[0], t.ctypes.data), h)
+
+
+def ns_relbin_edges(f_min: float, df: float, n_bins: int, eps: float = 0.25) -> np.ndarray:
+    """int32 coarse-bin edges [n_coarse + 1] (0, ..., n_bins) of the library's edge rule."""
+    n = C.c_int32()
+    code = _lib.ns_relbin_edges(float(f_min), float(df), int(n_bins), float(eps), None, 0, C.byref(n))
+    if n.value <= 0:
+        raise GwnsError(code, "ns_relbin_edges: bad grid or eps")
+    out = np.zeros(n.value, dtype=np.int32)
+    _check(_lib.ns_relbin_edges(float(f_min), float(df), int(n_bins), float(eps), out.ctypes.data, out.shape[0],
+                                C.byref(n)), None)
+    return out
 
 
 def ns_hrss_batch(h, event: int, live_u, u0, lnl0, lnl_star: float, n_steps: int, iteration: int = 0,

@@ -6,7 +6,6 @@ import sys
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import bench  # noqa: E402
-from paper_2509_04336_gb300 import relbin  # noqa: E402
 
 from _util import event  # noqa: E402
 
@@ -19,8 +18,9 @@ def test_oracle_walk_rate_counts_calls():
 
 
 def test_oracle_relbin_rate_counts_evaluations():
+    from oracle import relbin
     w, ev = event("four_param_2det_taylorf2", f_max=64.0)
-    edges = relbin.coarse_edges(ev.f_min, ev.df, ev.n_bins, 0.25)
+    edges = relbin.default_edges(ev.f_min, ev.df, ev.n_bins, 0.25)
     rate, info = bench.oracle_relbin_rate(w, ev, edges, budget_s=60.0, max_evals=3)
     assert info["evals"] == 3 and rate > 0
     assert f"{len(edges) - 1} coarse bins" in info["sample"]

@@ -7,7 +7,7 @@ in FP32 elementwise functions.  An FP32 accumulation error (~1e-6 relative) occa
 moves an activation across a bfloat16 rounding boundary (probability ~1e-6 / 2^-9 per
 activation, ~0.5 flips over the ~2000 activations of one point); one flip shifts ln q by
 about |w| 2^-9 ~ 1e-3 at most.  Hence: most points agree to 1e-4 in ln q, every point to
-2e-2; gradients (means over 300 points, where flips average out) to 2 % in norm."""
+2e-2; gradients (means over 300 points) element by element within the bound of gradient_bound."""
 import json
 import math
 import os
@@ -113,6 +113,25 @@ def test_flow_layers_and_round_trip():
     assert np.quantile(d, 0.9) < 1e-3 and d.max() < LOGQ_ALL
 
 
+def gradient_bound(f, u, og):
+    """Per-parameter tolerance of the GPU gradient (mean of -ln q over the points) against the
+    oracle's bf16 gradient og.  Both sides round the same operands to bfloat16; where an FP32
+    accumulation difference moves an operand across a bf16 rounding boundary, that operand
+    changes by one bf16 ulp (at most 2^-7 of its size), and the point's contribution c_ij to
+    parameter j by about as much relative to itself.  Bound: 2^-7 times the mean over points of
+    |c_ij| -- as if every point's contribution had moved by one ulp, which the flip rate (~0.5
+    flips among ~2000 operands of a point) makes far from tight -- plus 2^-10 |og_j| for the
+    FP32 accumulation and elementwise functions, plus a floor of 1e-9 of the largest |og|.  (The
+    unrounded FP64 gradient already leaves this bound at some parameters.)"""
+    C = np.stack([F.loss_and_grad(f, u[i:i + 1], bf16=True)[1] for i in range(u.shape[0])])
+    assert np.allclose(C.mean(axis=0), og, rtol=1e-9, atol=1e-12 * np.abs(og).max())
+    return 2.0 ** -7 * np.abs(C).mean(axis=0) + 2.0 ** -10 * np.abs(og) + 1e-9 * np.abs(og).max()
+
+
+def block_edges(D, L):
+    return np.cumsum([128 * D, 128, 128 * 128, 128, 2 * D * 128, 2 * D] * L)[:-1]
+
+
 def test_gradient_parity():
     w, ev, h = flow_handle("bbh11_3det_4s_taylorf2", layers=3)
     try:
@@ -125,13 +144,18 @@ def test_gradient_parity():
         gwns.ns_free(h)
     ol, og = F.loss_and_grad(f, u, bf16=True)
     assert abs(gl - ol) < 1e-4 * max(1.0, abs(ol))
-    err = np.linalg.norm(gg - og) / np.linalg.norm(og)
-    assert err < 2e-2, err
-    # every parameter block is exercised (no block left at zero)
-    blocks = np.split(og, np.cumsum([128 * D, 128, 128 * 128, 128, 2 * D * 128, 2 * D] * 3)[:-1])
-    gblocks = np.split(gg.astype(np.float64), np.cumsum([128 * D, 128, 128 * 128, 128, 2 * D * 128, 2 * D] * 3)[:-1])
-    for ob, gb in zip(blocks, gblocks):
-        assert np.linalg.norm(gb - ob) <= 5e-2 * np.linalg.norm(ob) + 1e-6
+    # element by element, every parameter
+    tol = gradient_bound(f, u, og)
+    d = np.abs(gg.astype(np.float64) - og)
+    bad = np.where(d > tol)[0]
+    assert bad.size == 0, f"{bad.size} parameters outside the bound, worst d/tol {np.max(d / tol):.2f} at {bad[:8]}"
+    # the bound is tight enough to catch a sign error: 2 |og_j| exceeds the tolerance of most
+    # parameters, and of at least 40 % in every block (the output layer's entries are means
+    # of contributions that largely cancel)
+    catch = 2.0 * np.abs(og) > tol
+    assert catch.mean() > 0.8
+    for cb in np.split(catch, block_edges(D, 3)):
+        assert cb.mean() > 0.4
 
 
 def test_training_matches_oracle_and_fits_gaussian():

@@ -71,6 +71,8 @@ def test_likelihood_parity(name, precision, tol):
         err = np.abs(got - want)
         # zero-noise truth has ln L = 0: an absolute floor of tol * SNR^2 / 2 there
         scale = np.maximum(np.abs(want), 0.5 * w.snr ** 2)
+        print(f"\nLNL_ERR {name} precision {precision}: max |err| / scale {np.max(err / scale):.3e}, "
+              f"max |err| {np.max(err):.3e}, points {th.shape[0]}")
         assert np.all(err <= tol * scale), f"max rel err {np.max(err / scale):.3e}"
     finally:
         gwns.ns_free(h)
@@ -131,12 +133,14 @@ def test_largest_batched_event_full_size():
     u = synth.uniform_unit_cube(12, w.n_dim, 31)
     th = np.ascontiguousarray(np.vstack([ev.theta_inj] + [P.transform(x, pri) for x in u]))
     want = np.array([L.log_likelihood(ev, t, w.waveform, w.use_ratio) for t in th])
-    for prec, tol in ((synth.PREC_FP64, TOL_FP64), (synth.PREC_MIXED_FF, TOL_MIXED)):
+    for prec, tol in ((synth.PREC_FP64, TOL_FP64), (synth.PREC_MIXED, TOL_MIXED), (synth.PREC_MIXED_FF, TOL_MIXED)):
         h = gwns.ns_init([gwns.make_config(w, pri, precision=prec)], [ev])
         try:
             got = np.zeros(th.shape[0])
             gwns.ns_likelihood_batch(h, 0, th, got)
             scale = np.maximum(np.abs(want), 0.5 * w.snr ** 2)
+            print(f"\nLNL_ERR batched64_16s precision {prec}: max |err| / scale "
+                  f"{np.max(np.abs(got - want) / scale):.3e}, max |err| {np.max(np.abs(got - want)):.3e}")
             assert np.all(np.abs(got - want) <= tol * scale), (prec, np.max(np.abs(got - want) / scale))
         finally:
             gwns.ns_free(h)
@@ -160,3 +164,29 @@ def test_largest_batched_event_full_size():
     assert np.array_equal(ga[same], oa[same]) and np.array_equal(gn[same], on[same])
     assert np.allclose(gu[same], ou[same], rtol=0, atol=1e-12)
     assert np.all(gl > star)
+
+
+@pytest.mark.parametrize("precision", [synth.PREC_FP64, synth.PREC_MIXED, synth.PREC_MIXED_FF])
+def test_likelihood_ratio_parity(precision):
+    # use_ratio (Sec. 4.1.1): ln Lambda = ln L + <d|d>/2 per detector sum, on the 11-parameter
+    # 3-detector event, in every precision; the kernels form it from <d|h> - <h|h>/2 directly.
+    from dataclasses import replace
+    w, ev = event("bbh11_3det_4s_taylorf2")
+    w = replace(w, use_ratio=True)
+    h = handle(w, ev, precision)
+    try:
+        _, th = prior_draws(w, ev, 64, 17)
+        th = np.ascontiguousarray(np.vstack([ev.theta_inj, th]))
+        got = np.zeros(th.shape[0])
+        gwns.ns_likelihood_batch(h, 0, th, got)
+        want = oracle_lnl(w, ev, th)
+        tol = TOL_FP64 if precision == synth.PREC_FP64 else TOL_MIXED
+        scale = np.maximum(np.abs(want), 0.5 * w.snr ** 2)
+        assert np.all(np.abs(got - want) <= tol * scale), f"max rel err {np.max(np.abs(got - want) / scale):.3e}"
+        # ln Lambda - ln L is the data term <d|d>/2, the same for every theta
+        plain = oracle_lnl(replace(w, use_ratio=False), ev, th[:3])
+        dd = 0.5 * sum(L.inner(d.data, d.data, d.psd, ev.df) for d in ev.detectors)
+        assert np.allclose(want[:3] - plain, dd, rtol=1e-12)
+        assert want[0] > 0.4 * w.snr ** 2   # the injection: ln Lambda near SNR^2 / 2
+    finally:
+        gwns.ns_free(h)

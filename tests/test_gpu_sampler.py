@@ -64,6 +64,27 @@ def test_sequential_mode_matches_oracle():
                                          nested.batch_delay(w.naccept - 1, 1), w.maxmcmc)
 
 
+def test_batches_with_likelihood_ratio_match_oracle():
+    # use_ratio (Sec. 4.1.1): the sampler runs on ln Lambda = ln L + <d|d>/2; eight batches
+    # follow the oracle's own run (same deletions, walks and evidence, which differs from the
+    # ln L run's by the constant <d|d>/2).
+    w, ev, pri, ll = tiny(use_ratio=True)
+    iters = 8
+    ref = oracle_run(w, pri, ll, max_iter=iters)
+    h = gwns.ns_init([gwns.make_config(w, pri, precision=synth.PREC_FP64, max_iter=iters)], [ev])
+    try:
+        code, prog = gwns.ns_step(h, iters)
+        th, lw = gwns.ns_posterior(h, 0)
+    finally:
+        gwns.ns_free(h)
+    p = prog[0]
+    assert p["iterations"] == iters and p["n_like"] == ref.n_like
+    nd = ref.dead_u.shape[0]
+    dead = np.stack([P.transform(u, pri) for u in ref.dead_u])
+    assert np.allclose(th[:nd], dead, rtol=1e-12, atol=1e-12)
+    assert abs(p["log_z"] - np.logaddexp.reduce(ref.dead_logw)) < 1e-9 * max(1.0, abs(p["log_z"]))
+
+
 @pytest.mark.parametrize("term_kind,term_value", [(synth.TERM_FRAC_REMAINING, 0.05),
                                                   (synth.TERM_DLOGZ, 0.3)])
 def test_run_to_termination_matches_oracle(term_kind, term_value):

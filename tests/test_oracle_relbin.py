@@ -85,13 +85,16 @@ def test_close_to_the_full_likelihood_in_the_posterior_bulk(name):
 
 @pytest.mark.parametrize("name", ["four_param_2det_taylorf2", "bbh11_3det_4s_taylorf2", "bbh11_3det_8s_phenomd"])
 def test_library_edges_follow_the_same_rule(name):
-    # The library's host-side edge rule (paper_2509_04336_gb300/relbin.py, written separately)
-    # gives the oracle's edges.
-    from paper_2509_04336_gb300 import relbin as R
+    # The library's edge rule (ns_relbin_edges, host code of libgwns, written separately) gives
+    # the oracle's edges; the call does no device work, so it runs without a GPU.
+    from paper_2509_04336_gb300 import build, gwns
+    build.build()
+    gwns.load()
     w = synth.workload(name)
     for eps in (0.1, 0.25, 1.0, 3.0):
-        assert np.array_equal(R.coarse_edges(w.f_min, w.df, w.n_bins, eps),
+        assert np.array_equal(gwns.ns_relbin_edges(w.f_min, w.df, w.n_bins, eps),
                               relbin.default_edges(w.f_min, w.df, w.n_bins, eps))
+    assert np.array_equal(gwns.ns_relbin_edges(w.f_min, w.df, 1, 0.25), [0, 1])
 
 
 @pytest.mark.parametrize("name", ["bbh11_3det_4s_taylorf2", "bbh11_3det_8s_phenomd"])
