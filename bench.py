@@ -35,20 +35,35 @@ from paper_2509_04336_gb300 import synth  # noqa: E402
 WORKLOAD = "bbh11_3det_4s_taylorf2"
 METRIC = "wall-time to logZ (|Δ|≤0.1 vs FP64 oracle); lnL evals/s vs plain FP64 walk"
 UNIT = "lnL evals/s"
-# Algorithmic FP32 flops per evaluated (walker, bin) of the float-float walk (FMA = 2):
-# phase over the 8-function basis as float-float (per term 1 mul + 3 FMA + 7 add = 14),
-# its reduction (2); per detector the exact time-shift reduction (9), sincospi (20, its
-# polynomial), the complex multiply-accumulate (6) and two Kahan updates (8): 114 + 3 * 43.
-FP32_FLOPS_PER_WALKER_BIN = 243.0
-# IMRPhenomD form, merger-ringdown bins (most of the band): phase over 3 basis terms (42) plus
-# the atan term (~20) and reduction (2), amplitude shape (~12), per detector 43 + the template
-# power update (6): 76 + 3 * 49.
-FP32_FLOPS_PER_WALKER_BIN_PD = 223.0
-FP32_PEAK_TFLOPS = 80.5      # nominal GB300 FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz
+# The method's own work per useful (walker, active bin) -- a bin of a likelihood call the chain
+# uses, not of a speculative proposal dropped after an earlier acceptance -- counted from the
+# formulas with an FMA as 2 flops, whatever precision carries it:
+#   TaylorF2: phase over the 8-function basis and its 2 log-type terms (25), per detector the
+#   time shift and range reduction (4), the amplitude (10), per detector the complex projection
+#   (6) and the compensated data-term update (12): 25 + 10 + 3 * (4 + 6 + 12) = 101 flops, and
+#   one sincos per detector (2 SFU ops each: 6).
+#   IMRPhenomD form (merger-ringdown bins, most of the band): 3 basis terms (6), the arctangent
+#   term (~20), the amplitude shape (~12), per detector time shift (4), projection (6), data
+#   term (12) and template-power update (6): 38 + 3 * 28 = 122 flops, and 6 SFU ops.
+ALG_FLOPS_PER_WALKER_BIN = {synth.TAYLORF2: 101.0, synth.PHENOMD_FORM: 122.0}
+ALG_SFU_PER_WALKER_BIN = 6.0
+# FP32 flops the float-float walk executes per evaluated (walker, bin), speculative proposals
+# included (the float-float emulation of the phase and sincospi's polynomial counted):
+#   TaylorF2: phase over 8 basis terms as float-float (14 each), reduction (2), per detector the
+#   exact time-shift reduction (9), sincospi (20), complex multiply-accumulate (6), two Kahan
+#   updates (8): 114 + 3 * 43 = 243.  IMRPhenomD form: 3 basis terms (42), arctangent (~20),
+#   reduction (2), amplitude shape (~12), per detector 43 + template power (6): 76 + 3 * 49 = 223.
+EXEC_FP32_FLOPS_PER_WALKER_BIN = {synth.TAYLORF2: 243.0, synth.PHENOMD_FORM: 223.0}
+# Plain FP64 walk: the same formula count carried in FP64 (its FP64 sincos not counted).
+FP64_ALG_FLOPS_PER_WALKER_BIN = {synth.TAYLORF2: 101.0, synth.PHENOMD_FORM: 122.0}
+FP32_PEAK_TFLOPS = 80.5      # GB300 FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 1.259     # GB300 FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz
 # DRAM bytes (read + write) of one walk launch, from one ncu capture of the current kernel
 # (walk_kernel_ff<3, WF>, batch 10 of the 4 s TaylorF2 workload and batch 3 of the 8 s
 # IMRPhenomD one); None for workloads without a capture of the current kernel.
 NCU_WALK_TRAFFIC_BYTES = {"bbh11_3det_4s_taylorf2": 246016 + 0, "bbh11_3det_8s_phenomd": 1646848 + 98560}
+# Workloads measured beside the headline in the default run (their own roofline, baseline, e2e).
+EXTRA_WORKLOADS = ("bbh11_3det_8s_phenomd", "batched64")
 
 
 def rank_info():
@@ -172,8 +187,10 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- oracle timing
 def oracle_walk_rate(w: synth.Workload, ev: synth.Event, budget_s: float, walkers: int = 4, steps: int = 8,
-                     max_rounds: int | None = None):
-    """lnL evals/s of the oracle's acceptance walk on this workload (single thread)."""
+                     max_rounds: int | None = None, round0: int = 0):
+    """lnL evals/s of the oracle's acceptance walk on this workload (single thread).  Rounds
+    round0, round0 + 1, ... are the walk's iteration counters, so processes given different
+    round0 walk different chains."""
     from oracle import likelihood as L, prior as P, walk
 
     pri = synth.priors_with_injection(w, ev)
@@ -185,7 +202,7 @@ def oracle_walk_rate(w: synth.Workload, ev: synth.Event, budget_s: float, walker
     n_like, t0, rounds = 0, time.perf_counter(), 0
     while True:
         _, _, _, nl, _ = walk.acceptance_walk(ll, surv[idx], lnl_s[idx], star, surv, steps,
-                                              P.periodic_mask(pri), (w.seed, 0), rounds)
+                                              P.periodic_mask(pri), (w.seed, 0), round0 + rounds)
         n_like += int(nl.sum())
         rounds += 1
         el = time.perf_counter() - t0
@@ -194,6 +211,49 @@ def oracle_walk_rate(w: synth.Workload, ev: synth.Event, budget_s: float, walker
     return n_like / el, {"evals": n_like, "seconds": el, "rounds": rounds,
                          "sample": f"{walkers} walkers x {steps} DE steps per round, {rounds} rounds, "
                                    f"{w.n_bins} bins x {len(w.detectors)} detectors"}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_pool(procs: int):
+    """A process pool for the oracle, started with spawn (never forked from a process that
+    holds a CUDA context)."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(procs)
+
+
+def oracle_walk_rate_all_cores(w: synth.Workload, ev: synth.Event, budget_s: float, pool=None, procs=None):
+    """lnL evals/s of the oracle's acceptance walk on every host core: one process per core,
+    each walking its own chains (different Philox iteration counters) for budget_s seconds;
+    rate = all processes' likelihood calls / the longest process time."""
+    procs = procs or host_cores()
+    own = pool is None
+    pool = oracle_pool(procs) if own else pool
+    try:
+        res = pool.starmap(oracle_walk_rate, [(w, ev, budget_s, 4, 8, None, 1000 * (i + 1)) for i in range(procs)])
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    evals = sum(r[1]["evals"] for r in res)
+    secs = max(r[1]["seconds"] for r in res)
+    rounds = sum(r[1]["rounds"] for r in res)
+    return evals / secs, {"evals": evals, "seconds": secs, "processes": procs,
+                          "sample": f"{procs} processes x (4 walkers x 8 DE steps per round), {rounds} rounds "
+                                    f"in all, {w.n_bins} bins x {len(w.detectors)} detectors"}
+
+
+def cpu_baseline(w: synth.Workload, ev: synth.Event, seconds: float, pool, procs: int):
+    """The oracle as it stands on the host: all cores (the reported value) and one core."""
+    rate_all, info_all = oracle_walk_rate_all_cores(w, ev, seconds, pool, procs)
+    rate_1, info_1 = oracle_walk_rate(w, ev, budget_s=max(1.0, seconds / 2))
+    return {"value": rate_all, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": info_all["sample"],
+            "single_core": {"value": rate_1, "unit": UNIT, "cores": 1, "sample": info_1["sample"]}}
 
 
 def oracle_relbin_rate(w: synth.Workload, ev: synth.Event, edges, budget_s: float, max_evals: int | None = None):
@@ -223,23 +283,29 @@ def run_reference(args):
     w = synth.workload(WORKLOAD)
     from oracle import likelihood as L
     ev = synth.make_event(w, L.project, L.inner)
-    step_rates = []
-    n_total, t_total = 0, 0.0
-    for i in range(args.warmup + args.steps):
-        rate, info = oracle_walk_rate(w, ev, budget_s=0.0, walkers=4, steps=8, max_rounds=1)
-        if i >= args.warmup:
-            n_total += info["evals"]
-            t_total += info["seconds"]
-            step_rates.append(rate)
+    procs = host_cores()
+    pool = oracle_pool(procs)
+    try:
+        pool.starmap(oracle_walk_rate, [(w, ev, 0.0, 1, 1, 1, 0)] * procs)   # start-up, untimed
+        n_total, t_total = 0, 0.0
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            res = pool.starmap(oracle_walk_rate, [(w, ev, 0.0, 4, 8, 1, 1000 * (p + 1) + i) for p in range(procs)])
+            el = time.perf_counter() - t0
+            if i >= args.warmup:
+                n_total += sum(r[1]["evals"] for r in res)
+                t_total += el
+    finally:
+        pool.close()
+        pool.join()
     value = n_total / t_total
+    sample = f"per step: {procs} processes x (4 walkers x 8 DE steps of the oracle), {WORKLOAD} event"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESCRIPTIONS[WORKLOAD], "precision": "FP64 (the oracle, numpy, CPU)",
-                       "step": "a bounded sample of the workload's walk: 4 walkers x 8 DE steps of the oracle",
-                       "events_per_rank": 1},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step: 4 walkers x 8 DE steps, bbh11_3det_4s_taylorf2 event"},
+                       "step": "a bounded sample of the workload's walk on every host core", "events_per_rank": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -303,7 +369,8 @@ def time_to_logz(gwns, device):
     """
     out = {}
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "logz_oracle.json")) as f:
-        golden = json.load(f)["four_param_2det_taylorf2"]
+        golden_all = json.load(f)
+    golden = golden_all["four_param_2det_taylorf2"]
     w4, ev4 = library_event(synth.workload("four_param_2det_taylorf2"), 0, device)
     for tag, prec in (("fp64", synth.PREC_FP64), ("float_float", synth.PREC_MIXED_FF)):
         r = run_to_logz(gwns, w4, ev4, prec, device)
@@ -319,25 +386,24 @@ def time_to_logz(gwns, device):
     out[WORKLOAD + "_float_float"] = dict(r, reference="plain FP64 walk on the GPU, same seed and data",
                                           reference_log_z=ref["log_z"], reference_seconds=ref["seconds"],
                                           abs_delta=d, within_0_1=d <= 0.1)
+    anchor = golden_all.get(WORKLOAD)
+    if anchor is not None:
+        # the oracle's own run of this configuration (all host cores, same seed)
+        d64 = abs(ref["log_z"] - anchor["log_z"])
+        out[WORKLOAD + "_fp64"] = dict(ref, reference="oracle (FP64 CPU), same seed", reference_log_z=anchor["log_z"],
+                                       reference_seconds=anchor["seconds"],
+                                       reference_processes=anchor.get("processes", 1), abs_delta=d64,
+                                       within_0_1=d64 <= 0.1)
     return out
 
 
-def run_ours(args):
+def measure_workload(gwns, name, steps, warmup, rank, world, local, dist, flush, sample_clocks=True, p_flow=None,
+                     with_fp64=True, cpu_seconds=10.0, pool=None, procs=1):
+    """One workload's line: the float-float walk timed over `steps` sampler batches after
+    `warmup` (lnL evals/s, CUDA events on the library's stream, L2 flushed between batches),
+    the FP64-phase and plain FP64 walks beside it, the walk's roofline on the method's own work,
+    the end-to-end figure through the public API with host buffers and the oracle baseline."""
     import torch
-
-    from paper_2509_04336_gb300 import build, gwns
-
-    rank, world, local = rank_info()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    if rank == 0:
-        build.build()
-    if dist is not None:
-        dist.barrier()
-    gwns.load()
 
     def barrier():
         if dist is not None:
@@ -350,17 +416,17 @@ def run_ours(args):
         dist.all_reduce(t, op=op)
         return float(t.item())
 
-    ws, evs = build_events(args.workload, rank, local)
+    MAX = dist.ReduceOp.MAX if dist else None
+    SUM = dist.ReduceOp.SUM if dist else None
+    ws, evs = build_events(name, rank, local)
     w, ev = ws[0], evs[0]
     ne = len(evs)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flow_run = name.endswith("_flow")
 
-    flow_run = args.workload.endswith("_flow")
-
-    def configs(precision, p_flow=None):
-        if flow_run and p_flow is None:
-            p_flow = args.p_flow
-        kw = {} if p_flow is None else {"p_flow": p_flow, "flow_layers": 8}
+    def configs(precision, pf=None):
+        if flow_run and pf is None:
+            pf = p_flow
+        kw = {} if pf is None else {"p_flow": pf, "flow_layers": 8}
         return [gwns.make_config(wi, synth.priors_with_injection(wi, ei), precision=precision, **kw)
                 for wi, ei in zip(ws, evs)]
 
@@ -370,20 +436,19 @@ def run_ours(args):
         out.update({k: progress[0][k] for k in ("walk_ms", "kernel_launches", "spec_depth", "n_steps", "mean_accept")})
         return out
 
-    def timed_steps(precision, steps, warmup, sample_clocks=False, p_flow=None):
-        h = gwns.ns_init(configs(precision, p_flow), evs, local)
+    def timed_steps(precision, clocks_on=False, pf=None):
+        h = gwns.ns_init(configs(precision, pf), evs, local)
         accepted = 0.0
         try:
             for _ in range(warmup):
                 gwns.ns_step(h, 1, ne)
             _, p0 = gwns.ns_step(h, 0, ne)
-            p0 = [total(p0)]
+            p0 = total(p0)
             ms = 0.0
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            clocks = ClockSampler(local) if sample_clocks else None
+            clocks = ClockSampler(local) if clocks_on else None
             barrier()
             torch.cuda.synchronize()
-            wall0 = time.perf_counter()
             if clocks:
                 clocks.__enter__()
             for _ in range(steps):
@@ -399,44 +464,34 @@ def run_ours(args):
                 clocks.__exit__()
             torch.cuda.synchronize()
             barrier()
-            wall = time.perf_counter() - wall0
             p1 = total(p)
-            res = {"ms": ms, "wall_s": wall, "evals": p1["n_like"] - p0[0]["n_like"],
-                   "bins": p1["n_bins"] - p0[0]["n_bins"], "walk_ms": p1["walk_ms"] - p0[0]["walk_ms"],
-                   "spec": p1["n_spec"] - p0[0]["n_spec"],
-                   "launches": p1["kernel_launches"] - p0[0]["kernel_launches"], "progress": p1,
-                   "accepted": accepted, "clocks": clocks.summary() if clocks else None}
-            return res
+            return {"ms": ms, "evals": p1["n_like"] - p0["n_like"], "bins": p1["n_bins"] - p0["n_bins"],
+                    "walk_ms": p1["walk_ms"] - p0["walk_ms"], "spec": p1["n_spec"] - p0["n_spec"],
+                    "launches": p1["kernel_launches"] - p0["kernel_launches"], "progress": p1,
+                    "accepted": accepted, "clocks": clocks.summary() if clocks else None}
         finally:
             gwns.ns_free(h)
 
-    mixed = timed_steps(synth.PREC_MIXED_FF, args.steps, args.warmup, sample_clocks=True)
-    sweep = None
+    def rate(r):
+        t = reduce(r["ms"], MAX)
+        return reduce(float(r["evals"]), SUM) / (t * 1e-3), t
+
+    mixed = timed_steps(synth.PREC_MIXED_FF, clocks_on=sample_clocks)
+    value, t_max = rate(mixed)
+    sweep = mixed64 = plain = None
     if flow_run:
         # the plain FP64 walk at 4000 live points takes seconds a batch: the flow line compares
         # proposals instead, every arm in the float-float mode
         sweep = {}
         for pf in (0.0, 0.5, 0.9):
-            r = mixed if pf == args.p_flow else timed_steps(synth.PREC_MIXED_FF, args.steps, args.warmup, p_flow=pf)
-            sweep[str(pf)] = {"lnl_evals_per_s": r["evals"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / args.steps,
+            r = mixed if pf == p_flow else timed_steps(synth.PREC_MIXED_FF, pf=pf)
+            sweep[str(pf)] = {"lnl_evals_per_s": r["evals"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / steps,
                               "accepted_steps_per_s": r["accepted"] / (r["ms"] * 1e-3),
                               "accepted_per_lnl_call": r["accepted"] / max(r["evals"], 1),
-                              "walk_ms_per_step": r["walk_ms"] / args.steps}
-        mixed64 = plain = None
-    else:
-        mixed64 = timed_steps(synth.PREC_MIXED, args.steps, args.warmup)
-        plain = timed_steps(synth.PREC_FP64, args.steps, args.warmup)
-
-    t_max = reduce(mixed["ms"], dist.ReduceOp.MAX if dist else None)
-    evals = reduce(float(mixed["evals"]), dist.ReduceOp.SUM if dist else None)
-    value = evals / (t_max * 1e-3)
-    value_plain = value_m64 = t_plain = t_m64 = None
-    if plain is not None:
-        t_plain = reduce(plain["ms"], dist.ReduceOp.MAX if dist else None)
-        evals_plain = reduce(float(plain["evals"]), dist.ReduceOp.SUM if dist else None)
-        value_plain = evals_plain / (t_plain * 1e-3)
-        t_m64 = reduce(mixed64["ms"], dist.ReduceOp.MAX if dist else None)
-        value_m64 = reduce(float(mixed64["evals"]), dist.ReduceOp.SUM if dist else None) / (t_m64 * 1e-3)
+                              "walk_ms_per_step": r["walk_ms"] / steps}
+    elif with_fp64:
+        mixed64 = timed_steps(synth.PREC_MIXED)
+        plain = timed_steps(synth.PREC_FP64)
 
     # end to end through the public API with host buffers: init (host data upload and the
     # initial live points), K batches, evidence read back
@@ -448,7 +503,7 @@ def run_ours(args):
     e0.record()
     h = gwns.ns_init(cfgs, [k[0] for k in keep], local)
     try:
-        for _ in range(args.steps):
+        for _ in range(steps):
             gwns.ns_step(h, 1, ne)
         evid = [gwns.ns_evidence(h, e) for e in range(ne)]
         _, pe = gwns.ns_step(h, 0, ne)
@@ -456,69 +511,174 @@ def run_ours(args):
         gwns.ns_free(h)
     e1.record()
     torch.cuda.synchronize()
-    lz, lz_err = evid[0][0], evid[0][1]
-    e2e_ms = reduce(e0.elapsed_time(e1), dist.ReduceOp.MAX if dist else None)
-    e2e_evals = reduce(float(sum(x[3] for x in evid)), dist.ReduceOp.SUM if dist else None)
-    h2d = sum(len(e.detectors) * e.n_bins * 3 * 8 for e in evs) / args.steps
+    e2e_ms = reduce(e0.elapsed_time(e1), MAX)
+    e2e_evals = reduce(float(sum(x[3] for x in evid)), SUM)
+    h2d = sum(len(e.detectors) * e.n_bins * 3 * 8 for e in evs) / steps
     d2h = (288 * ne + sum(2 * p["iterations"] * wi.num_delete * 8 + wi.n_live * 8 + 200 * 8
-                          for p, wi in zip(pe, ws))) / args.steps
-
+                          for p, wi in zip(pe, ws))) / steps
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return 0
+        return None
 
-    # roofline of the dominant kernel (the walk): algorithmic FP32 flops of every evaluated
-    # (walker, bin) -- speculative evaluations included -- over its event-timed duration
-    walk_launches = args.steps
-    walk_ms_avg = mixed["walk_ms"] / walk_launches
-    bins_evaluated = mixed["bins"] * mixed["spec"] / max(mixed["evals"], 1)
-    achieved = bins_evaluated * (FP32_FLOPS_PER_WALKER_BIN if w.waveform == synth.TAYLORF2
-                                 else FP32_FLOPS_PER_WALKER_BIN_PD) / (mixed["walk_ms"] * 1e-3) / 1e12
-    cpu_rate, cpu_info = oracle_walk_rate(w, ev, budget_s=args.cpu_seconds)
-    to_logz = time_to_logz(gwns, local) if (rank == 0 and args.workload == WORKLOAD) else None
-    if rank == 0 and flow_run and args.to_logz:
-        to_logz = flow_to_logz(gwns, w, ev, local)
-    fp32_flops = FP32_FLOPS_PER_WALKER_BIN if w.waveform == synth.TAYLORF2 else FP32_FLOPS_PER_WALKER_BIN_PD
-    clocks = mixed["clocks"] or {}
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESCRIPTIONS[args.workload],
+    wf = w.waveform
+    kname = f"walk_kernel_ff<{len(ev.detectors)},{wf}>"
+    # roofline of the dominant kernel (the walk) on the method's own work: useful (walker,
+    # active bin) pairs x the formula count, over the walk's event-timed duration
+    useful = float(mixed["bins"])
+    evaluated = useful * mixed["spec"] / max(mixed["evals"], 1)
+    walk_s = mixed["walk_ms"] * 1e-3
+    achieved = useful * ALG_FLOPS_PER_WALKER_BIN[wf] / walk_s / 1e12
+    roof = {"bound": "alu", "pipe": "fp32", "kernel": kname + " (float-float phase)",
+            "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "traffic": NCU_WALK_TRAFFIC_BYTES.get(name), "avg_launch_ms": mixed["walk_ms"] / steps,
+            "counted": f"{ALG_FLOPS_PER_WALKER_BIN[wf]:.0f} flops per useful (walker, active bin) "
+                       f"(speculative proposals dropped after an acceptance not counted), FMA = 2",
+            "useful_walker_bins_per_launch": useful / steps,
+            "sfu": {"achieved_tops": useful * ALG_SFU_PER_WALKER_BIN / walk_s / 1e12,
+                    "per_walker_bin": ALG_SFU_PER_WALKER_BIN},
+            "executed_fp32": {"achieved": evaluated * EXEC_FP32_FLOPS_PER_WALKER_BIN[wf] / walk_s / 1e12,
+                              "frac": evaluated * EXEC_FP32_FLOPS_PER_WALKER_BIN[wf] / walk_s / 1e12
+                              / FP32_PEAK_TFLOPS,
+                              "counted": f"{EXEC_FP32_FLOPS_PER_WALKER_BIN[wf]:.0f} FP32 flops per evaluated "
+                                         "(walker, bin), speculative proposals and the float-float emulation "
+                                         "included"},
+            "peak_source": "derived: GB300 FP32, 152 SMs x 128 lanes x 2 flop x 2.07 GHz (an FMA "
+                           "microbenchmark measured 74.7)"}
+    out = {
+        "value": value, "unit": UNIT, "ms_per_step": t_max / steps, "steps": steps, "warmup": warmup,
+        "config": {"workload": WORKLOAD_DESCRIPTIONS[name],
                    "precision": "mixed: FP32 sums, float-float phase, FP64 per-walker constants and lnL assembly",
                    "step": "one sampler batch (select, walk, insert)",
                    "l2": "flushed (256 MB write) between timed steps", "events_per_rank": ne},
-        "plain_fp64": None if plain is None else {"value": value_plain, "unit": UNIT,
-                                                  "ms_per_step": t_plain / args.steps},
-        "mixed_fp64_phase": None if plain is None else {"value": value_m64, "unit": UNIT,
-                                                        "ms_per_step": t_m64 / args.steps},
-        "mixed_over_plain": None if plain is None else value / value_plain,
-        "p_flow": args.p_flow if flow_run else None,
-        "p_flow_sweep": sweep,
+        "p_flow": p_flow if flow_run else None, "p_flow_sweep": sweep,
         "speculative_evals_per_eval": mixed["spec"] / max(mixed["evals"], 1),
         "spec_depth": mixed["progress"]["spec_depth"],
         "mean_walk_steps": mixed["progress"]["n_steps"], "mean_accept": mixed["progress"]["mean_accept"],
         "active_bins_per_eval": mixed["bins"] / max(mixed["evals"], 1),
         "e2e": {"value": e2e_evals / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "steps": args.steps, "log_z": lz, "log_z_err": lz_err},
+                "d2h_bytes_per_step": int(d2h), "steps": steps, "log_z": evid[0][0], "log_z_err": evid[0][1]},
         "gpu_launches": int(mixed["launches"]),
-        "roofline": {"bound": "alu", "pipe": "fp32",
-                     "kernel": f"walk_kernel_ff<3,{w.waveform}> (float-float phase)",
-                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": NCU_WALK_TRAFFIC_BYTES.get(args.workload),
-                     "avg_launch_ms": walk_ms_avg,
-                     "peak_source": "nominal GB300 FP32, 152 SMs x 128 lanes x 2 flop x 2.07 GHz; "
-                                    "FMA microbenchmark measured 74.7"},
-        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": cpu_info["sample"]},
-        "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
-                   "reasons": clocks.get("reasons", [])},
-        "time_to_logz": to_logz,
+        "roofline": roof,
+        "clocks": mixed["clocks"],
     }
+    if plain is not None:
+        vp, tp = rate(plain)
+        vm, tm = rate(mixed64)
+        ach64 = plain["bins"] * FP64_ALG_FLOPS_PER_WALKER_BIN[wf] / (plain["walk_ms"] * 1e-3) / 1e12
+        out["plain_fp64"] = {"value": vp, "unit": UNIT, "ms_per_step": tp / steps,
+                             "roofline": {"bound": "alu", "pipe": "fp64", "kernel": f"walk_kernel<0,{len(ev.detectors)},{wf}>",
+                                          "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                          "frac": ach64 / FP64_PEAK_TFLOPS,
+                                          "avg_launch_ms": plain["walk_ms"] / steps,
+                                          "counted": f"{FP64_ALG_FLOPS_PER_WALKER_BIN[wf]:.0f} FP64 flops per useful "
+                                                     "(walker, active bin), FP64 sincos not counted",
+                                          "peak_source": "derived: GB300 FP64, 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"},
+                             "spec_depth": plain["progress"]["spec_depth"]}
+        out["mixed_fp64_phase"] = {"value": vm, "unit": UNIT, "ms_per_step": tm / steps}
+        out["mixed_over_plain"] = value / vp
+    if pool is not None:
+        out["cpu_baseline"] = cpu_baseline(w, ev, cpu_seconds, pool, procs)
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2509_04336_gb300 import build, gwns
+
+    rank, world, local = rank_info()
+    dist = None
+    procs = host_cores()
+    # the oracle's process pool starts (spawn) before any CUDA work of this process
+    pool = oracle_pool(procs) if rank == 0 else None
+    try:
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        torch.cuda.set_device(local)
+        if rank == 0:
+            build.build()
+        if dist is not None:
+            dist.barrier()
+        gwns.load()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        head = measure_workload(gwns, args.workload, args.steps, args.warmup, rank, world, local, dist, flush,
+                                p_flow=args.p_flow, cpu_seconds=args.cpu_seconds, pool=pool, procs=procs)
+        extra = {}
+        if args.workload == WORKLOAD and not args.headline_only:
+            # the other configurations' lines, on fewer batches (the plain FP64 walk takes seconds
+            # a batch there)
+            xs, xw = max(3, min(args.steps, 5)), 3
+            for name in EXTRA_WORKLOADS:
+                extra[name] = measure_workload(gwns, name, xs, xw, rank, world, local, dist, flush,
+                                               sample_clocks=False, cpu_seconds=args.cpu_seconds / 2,
+                                               pool=pool, procs=procs)
+        if rank != 0:
+            return 0
+        to_logz = time_to_logz(gwns, local) if args.workload == WORKLOAD else None
+        if args.workload.endswith("_flow") and args.to_logz:
+            ws, evs = build_events(args.workload, 0, local)
+            to_logz = flow_to_logz(gwns, ws[0], evs[0], local)
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+    clocks = head.pop("clocks") or {}
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic"}
+    for k in ("config", "plain_fp64", "mixed_fp64_phase", "mixed_over_plain", "p_flow", "p_flow_sweep",
+              "speculative_evals_per_eval", "spec_depth", "mean_walk_steps", "mean_accept", "active_bins_per_eval",
+              "e2e", "gpu_launches", "roofline", "cpu_baseline"):
+        if k in head:
+            line[k] = head[k]
+    line["clocks"] = {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
+                      "reasons": clocks.get("reasons", [])}
+    line["time_to_logz"] = to_logz
+    for name, x in extra.items():
+        x.pop("clocks", None)
+        line[name] = x
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def run_logz_seeds(args):
+    """The metric's ln Z condition over many seeds: the headline configuration run to its
+    stopping rule in the float-float mode and with the plain FP64 walk on N independent noise
+    realisations and sampler seeds; the mean and standard error of ln Z(float-float) - ln Z(FP64)."""
+    import torch
+
+    from paper_2509_04336_gb300 import build, gwns
+
+    rank, world, local = rank_info()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    build.build()
+    gwns.load()
+    from dataclasses import replace
+    runs = []
+    for sd in range(args.logz_seeds):
+        w, ev = library_event(synth.workload(args.workload), sd, local)
+        w = replace(w, seed=synth.workload(args.workload).seed + sd)
+        ff = run_to_logz(gwns, w, ev, synth.PREC_MIXED_FF, local)
+        fp = run_to_logz(gwns, w, ev, synth.PREC_FP64, local)
+        runs.append({"seed_offset": sd, "log_z_ff": ff["log_z"], "log_z_fp64": fp["log_z"],
+                     "log_z_err_fp64": fp["log_z_err"], "delta": ff["log_z"] - fp["log_z"],
+                     "seconds_ff": ff["seconds"], "seconds_fp64": fp["seconds"],
+                     "n_like_ff": ff["n_like"], "n_like_fp64": fp["n_like"]})
+        print(json.dumps(runs[-1]), file=sys.stderr, flush=True)
+    d = np.array([r["delta"] for r in runs])
+    line = {"metric": "ln Z(float-float) - ln Z(plain FP64 walk), each run to its stopping rule",
+            "workload": WORKLOAD_DESCRIPTIONS[args.workload], "seeds": len(runs),
+            "mean_delta": float(d.mean()), "std_delta": float(d.std(ddof=1)) if d.size > 1 else None,
+            "stderr_mean_delta": float(d.std(ddof=1) / math.sqrt(d.size)) if d.size > 1 else None,
+            "mean_abs_delta": float(np.abs(d).mean()),
+            "mean_log_z_err": float(np.mean([r["log_z_err_fp64"] for r in runs])),
+            "mean_seconds_ff": float(np.mean([r["seconds_ff"] for r in runs])),
+            "mean_seconds_fp64": float(np.mean([r["seconds_fp64"] for r in runs])), "runs": runs}
+    print(json.dumps(line))
     return 0
 
 
@@ -599,8 +759,8 @@ def run_relbin(args):
     # roofline of the walk on the relative-binning path: the per-bin FP32 count of the waveform
     # for every grid bin an evaluation touched (edges and exact range), speculative ones included
     rb = arms["relbin"]
-    flops_bin = FP32_FLOPS_PER_WALKER_BIN if w.waveform == synth.TAYLORF2 else FP32_FLOPS_PER_WALKER_BIN_PD
-    touched = rb["_bins"] * rb["_spec"] / max(rb["_evals"], 1)
+    flops_bin = ALG_FLOPS_PER_WALKER_BIN[w.waveform]
+    touched = rb["_bins"]
     achieved = touched * flops_bin / (rb["_walk_ms"] * 1e-3) / 1e12
     for a in arms.values():
         for key in ("_bins", "_spec", "_evals", "_walk_ms"):
@@ -622,8 +782,9 @@ def run_relbin(args):
                      "kernel": f"walk_kernel_ff<3,{w.waveform}> (relative-binning path)",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                     "counted": "FP32 flops of the per-bin body for every grid bin touched (edges, exact "
-                                "range); the per-proposal constants are not counted"},
+                     "counted": f"{flops_bin:.0f} flops (the full path's per-bin formula count) for every grid "
+                                "bin a used evaluation touched (edges, exact range); speculative proposals and the "
+                                "per-proposal constants are not counted"},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_info["sample"]},
         "clocks": {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons", [])},
     }
@@ -637,7 +798,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="seconds of oracle work per process behind each cpu_baseline")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="measure only the headline workload (no 8 s and 64-event lines)")
     ap.add_argument("--profile-batches", type=int, default=0,
                     help="run this many batches of the workload without timing (a small case for ncu)")
     ap.add_argument("--precision", type=int, default=synth.PREC_MIXED_FF)
@@ -649,7 +813,11 @@ def main():
     ap.add_argument("--relbin", type=float, default=0.0,
                     help="eps [rad] > 0: the relative-binning line (full vs relative-binning likelihood) "
                          "on --workload instead of the headline line")
+    ap.add_argument("--logz-seeds", type=int, default=0,
+                    help="N > 0: run --workload to ln Z in float-float and plain FP64 on N seeds instead")
     args = ap.parse_args()
+    if args.logz_seeds > 0:
+        return run_logz_seeds(args)
     if args.relbin > 0.0:
         if args.workload == "batched64":
             ap.error("--relbin runs a single-event workload")
