@@ -14,7 +14,9 @@ Sathyaprakash 2009 (Eq. 3.18); aligned-spin terms (1.5PN and 2.5PN spin-orbit, 2
 (IMRPhenomD paper, Appendix B).  Pins: the Newtonian phase equals 3/128 (pi Mc f)^(-5/3),
 its frequency derivative gives the Newtonian chirp time, the phase is invariant under the
 exchange (m1, chi1) <-> (m2, chi2), and equal-mass phases depend on the spins only through
-chi_s and chi_a^2.  Higher-order coefficients beyond these invariants: parity unpinned.
+chi_s and chi_a^2.  Every coefficient a_k, a_k^l (k >= 2) is pinned independently by the
+stationary-phase derivation from the PN binding energy and flux of circular orbits, whose
+test-mass parts are the exact Kerr binding energy (tests/test_oracle_taylorf2_spa.py).
 """
 import math
 

@@ -85,19 +85,43 @@ def _int_v_power_log(m, A, B):
     return A * v ** (m + 1) / (m + 1) + B * (v ** (m + 1) * L / (m + 1) - v ** (m + 1) / (m + 1) ** 2)
 
 
+def _mul(a, b, n=8):
+    """Product of two truncated series in v (coefficient lists), to order v^(n-1)."""
+    out = [0] * n
+    for i, ai in enumerate(a):
+        if ai == 0:
+            continue
+        for j in range(n - i):
+            if b[j] != 0:
+                out[i + j] += ai * b[j]
+    return [sp.expand(c) for c in out]
+
+
 @functools.lru_cache(maxsize=None)
 def derived_coefficients():
-    """{k: (a_k, a_k^l)} of the stationary-phase phase, as sympy expressions."""
+    """{k: (a_k, a_k^l)} of the stationary-phase phase, as sympy expressions (L = ln v)."""
     e, f = energy_coeffs(), flux_coeffs()
-    # E(v) and F(v), x = v^2; dE/dv with L = ln v treated by d/dv = d/dv|_L + (1/v) d/dL
-    E = -(eta * v ** 2 / 2) * (1 + sum(ek * v ** k for k, ek in e.items()))
-    dE = sp.diff(E, v) + sp.diff(E, L) / v
-    Fbr = 1 + sum(fk * v ** k for k, fk in f.items())
-    # G = -E'/F = (5 / (32 eta)) v^-9 P(v): P to order v^7
-    P = sp.expand(sp.series(sp.expand(-dE / (eta * v)) / Fbr, v, 0, 8).removeO())
-    psi = 0
-    for k in range(8):
-        pk = sp.expand(P.coeff(v, k))
+    n = 8
+    # -E'(v) / (eta v) with E = -(eta v^2 / 2)(1 + sum e_k v^k):
+    # d/dv [v^(k+2) e_k] / 2 = (k + 2) e_k v^(k+1) / 2, plus the ln v derivative of e_k (none:
+    # the energy has no logarithm to this order)
+    num = [sp.Integer(1)] + [0] * (n - 1)
+    for k, ek in e.items():
+        assert not ek.has(L)
+        num[k] += sp.Rational(k + 2, 2) * ek
+    # 1 / (1 + u), u = sum f_k v^k: sum_j (-u)^j to order v^7
+    u = [0] * n
+    for k, fk in f.items():
+        u[k] = fk
+    inv = [sp.Integer(1)] + [0] * (n - 1)
+    term = [sp.Integer(1)] + [0] * (n - 1)
+    for _ in range(1, n):
+        term = _mul(term, [-c for c in u], n)
+        inv = [sp.expand(a + b) for a, b in zip(inv, term)]
+    P = _mul(num, inv, n)          # G = (5 / (32 eta)) v^-9 sum_k P_k v^k
+    out = {}
+    for k in range(n):
+        pk = sp.expand(P[k])
         A, B = pk.coeff(L, 0), pk.coeff(L, 1)
         assert sp.expand(pk - A - B * L) == 0
         # t: int v^(k-9) P_k,  phi: int v^(k-6) P_k; k = 5 in phi is the ln v case (no L there)
@@ -107,13 +131,12 @@ def derived_coefficients():
             Phi = A * L
         else:
             Phi = _int_v_power_log(k - 6, A, B)
-        psi += sp.Rational(5, 32) / eta * (2 * v ** 3 * T - 2 * Phi)
-    # in units of 3 / (128 eta v^5): the bracket sum_k (a_k + a_k^l L) v^k
-    bracket = sp.expand(psi * 128 * eta * v ** 5 / 3)
-    out = {}
-    for k in range(8):
-        ck = sp.expand(bracket.coeff(v, k))
-        out[k] = (sp.simplify(ck.coeff(L, 0)), sp.simplify(ck.coeff(L, 1)))
+        # Psi_k = (5 / (32 eta)) (2 v^3 T - 2 Phi), in units of 3 / (128 eta v^5): the bracket
+        # term (a_k + a_k^l L) v^k
+        br = sp.expand((2 * v ** 3 * T - 2 * Phi) * sp.Rational(5, 32) * sp.Rational(128, 3) * v ** 5)
+        assert sp.expand(br.subs(v, 1) * v ** k - br) == 0
+        br = br.subs(v, 1)
+        out[k] = (sp.expand(br.coeff(L, 0)), sp.expand(br.coeff(L, 1)))
     return out
 
 
