@@ -609,9 +609,11 @@ def run_ours(args):
             # a batch there)
             xs, xw = max(3, min(args.steps, 5)), 3
             for name in EXTRA_WORKLOADS:
+                # the 64-event population's plain FP64 walk takes ~35 s a batch: its FP64 arms are
+                # left to --workload batched64
                 extra[name] = measure_workload(gwns, name, xs, xw, rank, world, local, dist, flush,
                                                sample_clocks=False, cpu_seconds=args.cpu_seconds / 2,
-                                               pool=pool, procs=procs)
+                                               pool=pool, procs=procs, with_fp64=name != "batched64")
         if rank != 0:
             return 0
         to_logz = time_to_logz(gwns, local) if args.workload == WORKLOAD else None

@@ -83,6 +83,8 @@ extern "C" {
 
 #define NS_PROPOSAL_DE 0        /* differential-evolution steps only (Sec. 3.1)            */
 #define NS_PROPOSAL_DE_FLOW 1   /* DE steps mixed with flow independence proposals          */
+#define NS_PROPOSAL_HRSS 2      /* hit-and-run slice sampling as the inner kernel (Sec. 2.2, */
+                                /* Sec. 5; see ns_hrss_batch): hrss_moves moves a batch     */
 
 #define NS_PTR_HOST 0
 #define NS_PTR_DEVICE 1
@@ -122,7 +124,9 @@ typedef struct ns_config {
     int32_t flow_layers;  /* DE_FLOW: affine coupling layers, 1..16 (0: 8)            */
     int32_t flow_every;   /* DE_FLOW: retrain the flow every this many batches (0: 1)  */
     int32_t flow_epochs;  /* DE_FLOW: full-batch Adam steps per retraining (0: 50)     */
-    int32_t reserved;     /* must be 0                                              */
+    int32_t hrss_moves;   /* HRSS: slice-sampling moves per walker and batch, fixed (no
+                             walk-length retune; 0: 2 D).  Every event of a handle uses
+                             HRSS or none does.  Needs n_live - num_delete > D.          */
     double flow_lr;       /* DE_FLOW: Adam learning rate (0: 3e-3)                  */
 } ns_config;
 
@@ -225,8 +229,28 @@ int ns_walk_batch_noalloc(ns_handle* h, int event, const double* live_u, int n_l
 /* Run up to max_batches batches of the sampler on every unfinished event (Sec. 2.2.3,
  * Sec. 3.2): deletion, evidence update, walk, insertion, walk-length retune and the
  * termination test all run on the device.  progress is [n_events] (may be NULL).
- * Returns NS_OK when it ran; progress[e].done reports termination. */
+ * Returns NS_OK when it ran; progress[e].done reports termination.  NS_ETIMEOUT: the watchdog
+ * (ns_set_watchdog, ns_set_abort) ended walks early in a batch of this call; the batches ran to
+ * completion with the truncated walks (every walker still at a point above L*), the state is
+ * consistent and a later call continues the run.  With HRSS (NS_PROPOSAL_HRSS) each batch also
+ * forms the Cholesky factor of the survivors' covariance on the device; NS_EINVAL if it is not
+ * positive definite. */
 int ns_step(ns_handle* h, int max_batches, ns_progress* progress);
+
+/* Watchdog of the walks (failure detection on the device).  Every walk -- ns_walk_batch,
+ * ns_walk_batch_noalloc, ns_hrss_batch and the walks of ns_step -- checks between its rounds
+ * (HRSS: between moves) a time budget and an abort flag, and when either has run out it stops
+ * after the current round, keeps its current point (which satisfies L > L*) and reports
+ * NS_ETIMEOUT (host-pointer calls and ns_step; device-pointer walks return before the kernel
+ * runs, so their timeout shows in the next ns_step or host-pointer walk of the handle).
+ * ns_set_watchdog: budget_seconds > 0 bounds each walker's walk in wall time (GPU global timer,
+ * from the start of its thread block); 0 switches the budget off (the default).
+ * ns_set_abort: flag != 0 makes every running and later walk of the handle stop after its
+ * current round, until it is called again with 0.  ns_set_abort may be called from another host
+ * thread while ns_step runs (it writes the flag through a stream of its own and returns when the
+ * flag is on the device). */
+int ns_set_watchdog(ns_handle* h, double budget_seconds);
+int ns_set_abort(ns_handle* h, int flag);
 
 /* Final evidence of an event: the dead points plus the final live points, each with
  * weight L_i X / n_live.  log_z_err is the standard deviation of ln Z over replays
@@ -286,7 +310,7 @@ int ns_flow_grad(ns_handle* h, int event, const double* u, int n, float* grad, d
 int ns_flow_train(ns_handle* h, int event, const double* u, int n, int epochs, double* losses);
 
 /* ---- hit-and-run slice sampling (the inner kernel named in Sec. 2.2 and Sec. 5; Neal 2003) ----
- * One batch of the alternative inner kernel on an NS_PREC_FP64 handle, host arrays: n walkers
+ * One batch of the alternative inner kernel (the handle's precision), host arrays: n walkers
  * start at u0 [n][D] (unit cube) with ln L lnl0 [n] and each make n_steps slice-sampling moves
  * under ln L > lnl_star.  A move draws a line through the walker with direction C z / |z|
  * (z standard normal; C C^T the sample covariance of the survivors live_u [n_live_pts][D]),
@@ -297,8 +321,9 @@ int ns_flow_train(ns_handle* h, int event, const double* u, int n, int epochs, d
  * periodic coordinates wrap.  Random numbers: Philox4x64-10, key (seed, event), counters
  * (step, walker_offset + w, iteration, tag), tags 32..34 normals, 40 bracket, 48.. shrinkage.
  * Outputs: u_out [n][D], lnl_out [n], n_move [n] (moves made), n_like [n] (likelihood calls).
- * Errors: NS_EINVAL (other precision, bad sizes, a survivor covariance that is not positive
- * definite: n_live_pts must exceed D), NS_ENONFINITE, NS_ENOMEM, NS_ECUDA. */
+ * The walkers run on the GPU one CTA each, every candidate's likelihood summed by the whole CTA.
+ * Errors: NS_EINVAL (bad sizes, a survivor covariance that is not positive definite:
+ * n_live_pts must exceed D), NS_ENONFINITE, NS_ENOMEM, NS_ECUDA, NS_ETIMEOUT (watchdog). */
 int ns_hrss_batch(ns_handle* h, int event, const double* live_u, int n_live_pts,
                   const double* u0, const double* lnl0, double lnl_star, int n, int n_steps,
                   int64_t iteration, int64_t walker_offset, double* u_out, double* lnl_out,

@@ -72,8 +72,16 @@ static int check_config(const ns_config& c, int e) {
   if (c.num_delete < 1 || c.n_live - c.num_delete < 2)
     return set_error(nullptr, NS_EINVAL, "event %d: need 1 <= num_delete <= n_live - 2", e);
   if (c.naccept < 1 || c.maxmcmc < 1) return set_error(nullptr, NS_EINVAL, "event %d: naccept, maxmcmc >= 1", e);
-  if (c.spec_depth < 0 || c.spec_depth > kSpecMax || c.reserved != 0)
-    return set_error(nullptr, NS_EINVAL, "event %d: spec_depth must be in 0..%d (reserved 0)", e, kSpecMax);
+  if (c.spec_depth < 0 || c.spec_depth > kSpecMax)
+    return set_error(nullptr, NS_EINVAL, "event %d: spec_depth must be in 0..%d", e, kSpecMax);
+  if (c.proposal == NS_PROPOSAL_HRSS) {
+    if (c.hrss_moves < 0 || c.hrss_moves > 1000000)
+      return set_error(nullptr, NS_EINVAL, "event %d: hrss_moves must be in 0..1000000", e);
+    if (c.n_live - c.num_delete <= D)
+      return set_error(nullptr, NS_EINVAL, "event %d: HRSS needs n_live - num_delete > D = %d", e, D);
+  } else if (c.hrss_moves != 0) {
+    return set_error(nullptr, NS_EINVAL, "event %d: hrss_moves is for NS_PROPOSAL_HRSS (0 otherwise)", e);
+  }
   if (c.precision != NS_PREC_FP64 && c.precision != NS_PREC_MIXED && c.precision != NS_PREC_MIXED_FF)
     return set_error(nullptr, NS_EINVAL, "event %d: unknown precision %d", e, c.precision);
   if (c.waveform != NS_WAVEFORM_TAYLORF2 && c.waveform != NS_WAVEFORM_PHENOMD_FORM)
@@ -313,6 +321,8 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
     if (r) return r;
     if (cfg[e].precision != cfg[0].precision || cfg[e].waveform != cfg[0].waveform)
       return set_error(nullptr, NS_EINVAL, "every event of a handle needs the same precision and waveform");
+    if ((cfg[e].proposal == NS_PROPOSAL_HRSS) != (cfg[0].proposal == NS_PROPOSAL_HRSS))
+      return set_error(nullptr, NS_EINVAL, "every event of a handle uses HRSS (NS_PROPOSAL_HRSS) or none does");
     if (ev[e].n_det != ev[0].n_det)
       return set_error(nullptr, NS_EINVAL, "every event of a handle needs the same number of detectors");
   }
@@ -323,6 +333,7 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
   h->device = device;
   h->precision = cfg[0].precision;
   h->waveform = cfg[0].waveform;
+  h->hrss = cfg[0].proposal == NS_PROPOSAL_HRSS;
   h->events.resize(n_events);
   int max_det = 0;
   for (int e = 0; e < n_events; ++e) {
@@ -331,7 +342,8 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
     max_det = ev[e].n_det > max_det ? ev[e].n_det : max_det;
   }
   h->max_det = max_det;
-  if ((e0 = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+  if ((e0 = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e0 = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking)) != cudaSuccess) {
     ns_free(h);
     return set_error(nullptr, NS_ECUDA, "stream: %s", cudaGetErrorString(e0));
   }
@@ -342,7 +354,8 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
   std::vector<EventDev> tab(n_events);
   for (int e = 0; e < n_events; ++e) tab[e] = h->events[e].dev;
   if ((e0 = cudaMemcpy(h->d_events, tab.data(), sizeof(EventDev) * n_events, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e0 = cudaMalloc(&h->d_status, sizeof(int32_t) * 4)) != cudaSuccess) {
+      (e0 = cudaMalloc(&h->d_status, sizeof(int32_t) * 4)) != cudaSuccess ||
+      (e0 = cudaMemset(h->d_status, 0, sizeof(int32_t) * 4)) != cudaSuccess) {
     ns_free(h);
     return set_error(nullptr, NS_ECUDA, "event table upload: %s", cudaGetErrorString(e0));
   }
@@ -474,8 +487,9 @@ extern "C" int ns_walk_batch(ns_handle* h, int event, const double* live_u, int 
   T.done = 0;
   T.event = event;
   T.spec = E.cfg.spec_depth > 0 ? E.cfg.spec_depth : default_spec(h->precision);
+  watchdog_fields(h, T);
   cudaError_t e;
-  if ((e = cudaMemsetAsync(h->d_status + 1, 0, sizeof(int32_t), s)) != cudaSuccess) return cuda_fail(h, e, "status reset");
+  if ((e = cudaMemsetAsync(h->d_status + 1, 0, sizeof(int32_t) * 2, s)) != cudaSuccess) return cuda_fail(h, e, "status reset");
   int fr = flow_attach(h, event, T, n, n_steps, &h->scratch_flow, s);
   if (fr) return fr;
   // block -> (event, walker) maps, one task slot of the handle
@@ -515,6 +529,7 @@ extern "C" int ns_walk_batch(ns_handle* h, int event, const double* live_u, int 
         (e = cudaMemcpyAsync(n_like, d_nl, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s)))
       return cuda_fail(h, e, "D2H walk outputs");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "walk");
+    if ((r = watchdog_report(h))) return r;
     for (int j = 0; j < n; ++j) if (n_accept[j] == 0) return NS_WMAXMCMC;
     return NS_OK;
   }
@@ -527,6 +542,46 @@ extern "C" int ns_walk_batch(ns_handle* h, int event, const double* live_u, int 
     return cuda_fail(h, e, "H2D walk task");
   e = launch_walk(h->precision, h->waveform, E.n_det, h->d_events, d_task, d_be, d_bl, n, s);
   return e == cudaSuccess ? NS_OK : cuda_fail(h, e, "walk launch");
+}
+
+// The watchdog fields of a walk task: the handle's abort flag (d_status[3]), its timeout bit
+// (d_status[2]) and its time budget.
+void watchdog_fields(ns_handle* h, WalkTask& T) {
+  T.abort = h->d_status + 3;
+  T.status = h->d_status + 2;
+  T.budget_ns = h->budget_ns;
+}
+
+// NS_ETIMEOUT when a walk of the handle stopped on its watchdog since the bit was last cleared.
+int watchdog_report(ns_handle* h) {
+  int32_t st = 0;
+  cudaError_t e = cudaMemcpy(&st, h->d_status + 2, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "watchdog status");
+  if (st) return set_error(h, NS_ETIMEOUT, "a walk stopped on the watchdog (time budget or abort flag)");
+  return NS_OK;
+}
+
+extern "C" int ns_set_watchdog(ns_handle* h, double budget_seconds) {
+  if (!h) return set_error(nullptr, NS_EINVAL, "handle is NULL");
+  if (!(budget_seconds >= 0.0) || !(budget_seconds < 1e9)) return set_error(h, NS_EINVAL, "budget must be in [0, 1e9) s");
+  cudaSetDevice(h->device);
+  cudaGetLastError();
+  h->budget_ns = (uint64_t)(budget_seconds * 1e9);
+  if (budget_seconds > 0.0 && h->budget_ns == 0) h->budget_ns = 1;
+  // the sampler's tasks read it at every batch
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  for (size_t ev = 0; ev < h->events.size() && e == cudaSuccess && h->d_tasks; ++ev)
+    e = cudaMemcpy(&h->d_tasks[ev].budget_ns, &h->budget_ns, sizeof(uint64_t), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? NS_OK : cuda_fail(h, e, "watchdog budget");
+}
+
+extern "C" int ns_set_abort(ns_handle* h, int flag) {
+  if (!h) return set_error(nullptr, NS_EINVAL, "handle is NULL");
+  cudaSetDevice(h->device);
+  const int32_t v = flag ? 1 : 0;
+  cudaError_t e = cudaMemcpyAsync(h->d_status + 3, &v, sizeof(int32_t), cudaMemcpyHostToDevice, h->aux_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->aux_stream);
+  return e == cudaSuccess ? NS_OK : set_error(h, NS_ECUDA, "abort flag: %s", cudaGetErrorString(e));
 }
 
 extern "C" void ns_free(ns_handle* h) {
@@ -545,6 +600,7 @@ extern "C" void ns_free(ns_handle* h) {
   cudaFree(h->scratch_map.ptr);
   cudaFree(h->scratch_flow.ptr);
   if (h->stream) cudaStreamDestroy(h->stream);
+  if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
   delete h;
 }
 

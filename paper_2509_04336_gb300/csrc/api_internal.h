@@ -28,6 +28,8 @@ struct NsState {
   int64_t n_dead, n_like, iteration, max_iter, dead_cap, n_bins_eval, n_spec_eval;
   int32_t n_live, k, D, n_steps, naccept, maxmcmc, term_kind, done, zero_accept, overflow;
   int32_t spec, spec_auto, spec_cap, spec_rule;   // spec = min(spec_rule, spec_cap)
+  int32_t hrss;        // HRSS inner kernel: moves per walker and batch (0: the DE walk)
+  int32_t chol_bad;    // HRSS: the survivors' covariance was not positive definite
   uint64_t key0, key1;
   double* live_u;      // [n_live][D]
   double* live_lnl;    // [n_live]
@@ -46,6 +48,7 @@ struct NsState {
   double* dead_lnl;    // [dead_cap]
   double* dead_logw;   // [dead_cap]
   int32_t* dead_nlive; // [dead_cap]
+  double* chol;        // HRSS: [D][D] lower Cholesky factor of the survivors' covariance
 };
 
 struct EventHost {
@@ -76,6 +79,9 @@ struct ns_handle {
   int waveform = 0;
   int max_det = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t aux_stream = nullptr;   // ns_set_abort's writes, not ordered with the walks
+  bool hrss = false;                   // every event uses the HRSS inner kernel
+  uint64_t budget_ns = 0;              // watchdog time budget of a walk (0: none)
   std::vector<gwns::EventHost> events;
   gwns::EventDev* d_events = nullptr;
   int32_t* d_status = nullptr;
@@ -103,6 +109,8 @@ struct ns_handle {
 };
 
 int set_error(ns_handle* h, int code, const char* fmt, ...);
+void watchdog_fields(ns_handle* h, gwns::WalkTask& T);
+int watchdog_report(ns_handle* h);
 int cuda_fail(ns_handle* h, cudaError_t e, const char* what);
 int ensure_scratch(ns_handle* h, gwns::Scratch& s, size_t bytes);
 int nested_init(ns_handle* h);

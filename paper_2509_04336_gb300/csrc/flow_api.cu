@@ -75,9 +75,9 @@ int check_err_flag(ns_handle* h, cudaStream_t s, const char* what) {
 
 // ---------------------------------------------------------------- setup and teardown
 int flow_check_config(const ns_config& c, int e) {
-  if (c.proposal != NS_PROPOSAL_DE && c.proposal != NS_PROPOSAL_DE_FLOW)
+  if (c.proposal != NS_PROPOSAL_DE && c.proposal != NS_PROPOSAL_DE_FLOW && c.proposal != NS_PROPOSAL_HRSS)
     return set_error(nullptr, NS_EINVAL, "event %d: unknown proposal %d", e, c.proposal);
-  if (c.proposal == NS_PROPOSAL_DE) return NS_OK;
+  if (c.proposal != NS_PROPOSAL_DE_FLOW) return NS_OK;
   if (!(c.p_flow >= 0.0 && c.p_flow <= 1.0)) return set_error(nullptr, NS_EINVAL, "event %d: p_flow must be in [0, 1]", e);
   if (c.flow_layers < 0 || c.flow_layers > kFlowMaxLayers)
     return set_error(nullptr, NS_EINVAL, "event %d: flow_layers must be in 0..%d", e, kFlowMaxLayers);

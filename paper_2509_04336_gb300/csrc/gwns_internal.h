@@ -43,6 +43,15 @@ struct WalkTask {
   double p_flow;
   int32_t f_stride;
   int32_t pad_;
+  // hit-and-run slice sampling (HRSS) tasks: the lower Cholesky factor [D][D] of the
+  // survivors' covariance; n_steps counts moves
+  const double* chol;
+  // watchdog: a walk ends after the round in which *abort is nonzero or more than budget_ns
+  // nanoseconds (globaltimer) have passed since its CTA started (0: no budget); it then sets
+  // bit 0 of *status (null pointers: no watchdog)
+  const int32_t* abort;
+  int32_t* status;
+  uint64_t budget_ns;
 };
 
 constexpr int kSpecMax = 32;   // speculation depth limit (one warp of proposals)
@@ -58,11 +67,10 @@ cudaError_t launch_unit_to_theta(const EventDev* d_ev, const double* d_u, int64_
 // no_cutoff: continue the template above its cutoff (the relative-binning fiducial).
 cudaError_t launch_waveform(int waveform, int n_det, const EventDev* d_ev, const double* d_theta, int n, int n_bins,
                             double* d_hre, double* d_him, cudaStream_t s, int no_cutoff = 0);
-// n walkers x n_steps hit-and-run slice-sampling moves (FP64); d_chol [D][D] lower-triangular.
-cudaError_t launch_hrss(int waveform, int n_det, const EventDev* d_ev, const double* d_chol, const double* d_u0,
-                        const double* d_lnl0, double lnl_star, int n, int n_steps, uint64_t iteration,
-                        int64_t walker_offset, uint64_t key0, uint64_t key1, double* d_uo, double* d_lo,
-                        int32_t* d_nm, int32_t* d_nl, cudaStream_t s);
+// Block b makes the HRSS moves of walker blk_local[b] of task blk_task[b] (the task's chol,
+// n_steps moves; n_acc receives the moves made).
+cudaError_t launch_hrss(int precision, int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
+                        const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s);
 // Block b walks walker blk_local[b] of task blk_task[b].
 cudaError_t launch_walk(int precision, int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
                         const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s);

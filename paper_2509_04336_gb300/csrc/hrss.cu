@@ -1,7 +1,8 @@
 // hrss.cu -- ns_hrss_batch: one batch of hit-and-run slice-sampling moves (the inner kernel
 // the paper names as the vectorised framework's original choice, Sec. 2.2, and as the way
 // forward for GPU-native inner kernels, Sec. 5).  The host forms the Cholesky factor of the
-// survivors' covariance (D <= 11, FP64) and the FP64 kernel hrss_kernel runs the moves.
+// survivors' covariance (D <= 11, FP64) and hrss_kernel (the handle's precision) runs the moves;
+// inside ns_step the same kernel runs after chol_kernel forms the factor on the device.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -17,7 +18,6 @@ extern "C" int ns_hrss_batch(ns_handle* h, int event, const double* live_u, int 
                              int32_t* n_like) {
   if (!h) return set_error(nullptr, NS_EINVAL, "handle is NULL");
   if (event < 0 || event >= (int)h->events.size()) return set_error(h, NS_EINVAL, "event out of range");
-  if (h->precision != NS_PREC_FP64) return set_error(h, NS_EINVAL, "hit-and-run slice sampling runs in NS_PREC_FP64");
   if (n < 0 || n_steps < 0 || n_live_pts < 2 || iteration < 0 || walker_offset < 0)
     return set_error(h, NS_EINVAL, "need n >= 0, n_steps >= 0, n_live_pts >= 2, iteration >= 0, walker_offset >= 0");
   if (n > 0 && (!live_u || !u0 || !lnl0 || !u_out || !lnl_out || !n_move || !n_like))
@@ -58,26 +58,51 @@ extern "C" int ns_hrss_batch(ns_handle* h, int event, const double* live_u, int 
   cudaSetDevice(h->device);
   cudaGetLastError();
   cudaStream_t s = h->stream;
-  const size_t in_b = sizeof(double) * ((size_t)D * D + nu + n);
+  // task, block maps, factor and starts in one upload; outputs in the output scratch
+  WalkTask T;
+  std::memset(&T, 0, sizeof(T));
+  T.lnl_star = lnl_star;
+  T.iteration = iteration;
+  T.walker_offset = walker_offset;
+  T.key0 = E.cfg.seed;
+  T.key1 = (uint64_t)event;
+  T.n_s = n_live_pts;
+  T.n = n;
+  T.n_steps = n_steps;
+  T.event = event;
+  T.spec = 1;
+  watchdog_fields(h, T);
+  const size_t task_b = (sizeof(WalkTask) + 255) / 256 * 256;
+  const size_t maps_b = (2 * sizeof(int32_t) * (size_t)n + 255) / 256 * 256;
+  const size_t in_b = task_b + maps_b + sizeof(double) * ((size_t)D * D + nu + n);
   const size_t out_b = sizeof(double) * (nu + n) + 2 * sizeof(int32_t) * n;
   int r;
   if ((r = ensure_scratch(h, h->scratch_in, in_b))) return r;
   if ((r = ensure_scratch(h, h->scratch_out, out_b))) return r;
-  double* d_chol = (double*)h->scratch_in.ptr;
+  char* base = (char*)h->scratch_in.ptr;
+  WalkTask* d_task = (WalkTask*)base;
+  int32_t* d_bt = (int32_t*)(base + task_b);
+  int32_t* d_bl = d_bt + n;
+  double* d_chol = (double*)(base + task_b + maps_b);
   double* d_u0 = d_chol + (size_t)D * D;
   double* d_l0 = d_u0 + nu;
   double* d_uo = (double*)h->scratch_out.ptr;
   double* d_lo = d_uo + nu;
   int32_t* d_nm = (int32_t*)(d_lo + n);
   int32_t* d_nl = d_nm + n;
+  T.chol = d_chol; T.u0 = d_u0; T.lnl0 = d_l0; T.u_out = d_uo; T.lnl_out = d_lo; T.n_acc = d_nm; T.n_like = d_nl;
+  std::vector<char> stage(task_b + maps_b, 0);
+  std::memcpy(stage.data(), &T, sizeof(T));
+  int32_t* bt = (int32_t*)(stage.data() + task_b);
+  for (int j = 0; j < n; ++j) { bt[j] = 0; bt[n + j] = j; }
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(d_chol, L.data(), sizeof(double) * L.size(), cudaMemcpyHostToDevice, s)) ||
+  if ((e = cudaMemsetAsync(h->d_status + 2, 0, sizeof(int32_t), s)) ||
+      (e = cudaMemcpyAsync(base, stage.data(), stage.size(), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(d_chol, L.data(), sizeof(double) * L.size(), cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(d_u0, u0, sizeof(double) * nu, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(d_l0, lnl0, sizeof(double) * n, cudaMemcpyHostToDevice, s)))
     return cuda_fail(h, e, "H2D hrss inputs");
-  if ((e = launch_hrss(h->waveform, E.n_det, h->d_events + event, d_chol, d_u0, d_l0, lnl_star, n, n_steps,
-                       (uint64_t)iteration, walker_offset, E.cfg.seed, (uint64_t)event, d_uo, d_lo, d_nm, d_nl, s)) !=
-      cudaSuccess)
+  if ((e = launch_hrss(h->precision, h->waveform, E.n_det, h->d_events, d_task, d_bt, d_bl, n, s)) != cudaSuccess)
     return cuda_fail(h, e, "hrss launch");
   if ((e = cudaMemcpyAsync(u_out, d_uo, sizeof(double) * nu, cudaMemcpyDeviceToHost, s)) ||
       (e = cudaMemcpyAsync(lnl_out, d_lo, sizeof(double) * n, cudaMemcpyDeviceToHost, s)) ||
@@ -85,5 +110,5 @@ extern "C" int ns_hrss_batch(ns_handle* h, int event, const double* live_u, int 
       (e = cudaMemcpyAsync(n_like, d_nl, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s)))
     return cuda_fail(h, e, "D2H hrss outputs");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "hrss");
-  return NS_OK;
+  return watchdog_report(h);
 }

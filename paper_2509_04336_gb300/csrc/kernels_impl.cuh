@@ -33,6 +33,19 @@ __device__ __forceinline__ float top52_half_f(uint64_t x) {
   return fmaf(__uint2float_rn((uint32_t)(v >> 20)), 1048576.0f, __uint2float_rn((uint32_t)(v & 0xFFFFFull)) + 0.5f);
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The watchdog test of a walk's thread 0: a host-set abort flag, or the task's time budget
+// (nanoseconds since the CTA started) spent.
+__device__ __forceinline__ bool walk_should_stop(const WalkTask& T, uint64_t t0) {
+  if (T.abort && *(volatile const int32_t*)T.abort != 0) return true;
+  return T.budget_ns != 0ull && global_ns() - t0 > T.budget_ns;
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   float bb = s - a;
@@ -690,6 +703,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
   double lnl = T.lnl0[j];
   int n_acc = 0, n_like = 0;
   int64_t n_bins = 0, n_spec = 0;
+  const uint64_t t0 = threadIdx.x == 0 ? global_ns() : 0ull;
   const double de_scale = 2.38 / sqrt(2.0 * (double)D);
   const float de_scale32 = (float)de_scale;
   __syncthreads();
@@ -900,6 +914,10 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
         }
       }
       n_spec += nin;
+      if (walk_should_stop(T, t0)) {   // watchdog: end the walk after this round
+        nxt = n_steps;
+        if (T.status) atomicOr(T.status, 1);
+      }
       s_next = nxt;
     }
     __syncthreads();
@@ -1005,6 +1023,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   double lnl = T.lnl0[j];
   int n_acc = 0, n_like = 0;
   int64_t n_bins = 0, n_spec = 0;
+  const uint64_t t0 = threadIdx.x == 0 ? global_ns() : 0ull;
   const ff de_scale = ff_from_double(2.38 / sqrt(2.0 * (double)D));
   __syncthreads();
   const int sw = s_setup_warp;
@@ -1226,6 +1245,10 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
             else s_needq = 1;
           }
         }
+        if (walk_should_stop(T, t0)) {   // watchdog: end the walk after this round
+          nxt = n_steps;
+          if (T.status) atomicOr(T.status, 1);
+        }
         s_next = nxt;
       }
     }
@@ -1248,49 +1271,61 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
 }
 
 // ---------------------------------------------------------------- hit-and-run slice sampling
-// FP64 (mode 0).  One CTA per walker; thread 0 runs each move's slice logic and the whole CTA
-// evaluates every in-bounds candidate's ln L.  A move (Neal 2003, stepping out and shrinkage,
-// along a random line): direction d = C z / |z| (z standard normal, C the Cholesky factor of
-// the survivors' covariance), bracket [lo, lo + 1] with lo = -U, stepping out by one unit at a
-// time with a budget of kHrssMaxOut - 1 split as J = floor(kHrssMaxOut V) to the left and the
-// rest to the right while the bracket's end is inside the slice, then shrinkage draws until a
-// point inside the slice (at most kHrssMaxShrink; then the walker stays).  A candidate outside
-// the cube costs no likelihood call; periodic coordinates wrap.  Philox blocks (step, walker,
-// iteration, tag): tags 32 + c the normals (Box-Muller on words (0, 1) and (2, 3)), 40 the
-// bracket (U, V), 48 + j / 4 word j % 4 the j-th shrinkage uniform.
+// Any precision.  One CTA per walker (block b: walker blk_local[b] of task blk_task[b]); thread 0
+// runs each move's slice logic and the whole CTA evaluates every in-bounds candidate's ln L (the
+// likelihood of the handle's precision; relative binning on warp 0 when the event uses it).  A
+// move (Neal 2003, stepping out and shrinkage, along a random line): direction d = C z / |z|
+// (z standard normal, C = task.chol, the Cholesky factor of the survivors' covariance), bracket
+// [lo, lo + 1] with lo = -U, stepping out by one unit at a time with a budget of kHrssMaxOut - 1
+// split as J = floor(kHrssMaxOut V) to the left and the rest to the right while the bracket's
+// end is inside the slice, then shrinkage draws until a point inside the slice (at most
+// kHrssMaxShrink; then the walker stays).  A candidate outside the cube costs no likelihood
+// call; periodic coordinates wrap.  Philox blocks (step, walker, iteration, tag): tags 32 + c
+// the normals (Box-Muller on words (0, 1) and (2, 3)), 40 the bracket (U, V), 48 + j / 4 word
+// j % 4 the j-th shrinkage uniform.  task.n_steps moves; n_acc receives the moves made,
+// n_like the likelihood calls; the watchdog (task.abort, task.budget_ns) is checked before
+// every move.
 constexpr int kHrssMaxOut = 10;
 constexpr int kHrssMaxShrink = 100;
 
-template <int NDET, int WF>
-__global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restrict__ evp,
-                                                         const double* __restrict__ chol,
-                                                         const double* __restrict__ u0,
-                                                         const double* __restrict__ lnl0, double lnl_star,
-                                                         int n_steps, uint64_t it, int64_t walker_offset,
-                                                         uint64_t key0, uint64_t key1, double* __restrict__ u_out,
-                                                         double* __restrict__ lnl_out, int32_t* __restrict__ n_move,
-                                                         int32_t* __restrict__ n_like) {
+template <int PREC, int NDET, int WF>
+__global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restrict__ evs, WalkTask* tasks,
+                                                         const int32_t* __restrict__ blk_task,
+                                                         const int32_t* __restrict__ blk_local) {
   __shared__ WalkerParams P;
   __shared__ double red[kWarps][kMaxVals];
   __shared__ double vals[kMaxVals];
   __shared__ double x[kMaxDim], dvec[kMaxDim], pt[kMaxDim];
-  __shared__ int s_eval, s_end;
-  const EventDev& ev = *evp;
+  __shared__ double s_rbl;
+  __shared__ int s_eval, s_end, s_stop, s_rbk;
+  const WalkTask& T = tasks[blk_task[blockIdx.x]];
+  const int j = blk_local[blockIdx.x];
+  const EventDev& ev = evs[T.event];
+  if (T.done) return;
   const int D = ev.n_dim;
-  const int j = blockIdx.x;
-  const uint64_t wid = (uint64_t)(walker_offset + j);
-  if ((int)threadIdx.x < D) x[threadIdx.x] = u0[(size_t)j * D + threadIdx.x];
-  double lnl = lnl0[j];
+  const int n_steps = T.n_steps;
+  const double lnl_star = T.lnl_star;
+  const uint64_t it = (uint64_t)T.iteration;
+  const uint64_t wid = (uint64_t)(T.walker_offset + j);
+  const double* chol = T.chol;
+  bool rb = false;
+  if constexpr (PREC == 2) rb = ev.rb_nb > 0;
+  if ((int)threadIdx.x < D) x[threadIdx.x] = T.u0[(size_t)j * D + threadIdx.x];
+  double lnl = T.lnl0[j];
   int moves = 0, calls = 0;
+  int64_t n_bins = 0;
+  const uint64_t t0 = threadIdx.x == 0 ? global_ns() : 0ull;
   // thread 0's state of the current move: phase 0 steps out left, 1 right, 2 shrinks
   double lo = 0.0, hi = 0.0, tc = 0.0;
   int phase = 2, jl = 0, kr = 0, nsh = 0;
   __syncthreads();
   for (int t = 0; t < n_steps; ++t) {
     if (threadIdx.x == 0) {
+      s_stop = walk_should_stop(T, t0) ? 1 : 0;
+      if (s_stop && T.status) atomicOr(T.status, 1);
       double z[kMaxDim];
       for (int c = 0; 4 * c < D; ++c) {
-        const Philox4 b = philox4x64((uint64_t)t, wid, it, 32ull + (uint64_t)c, key0, key1);
+        const Philox4 b = philox4x64((uint64_t)t, wid, it, 32ull + (uint64_t)c, T.key0, T.key1);
         for (int q = 0; q < 2; ++q) {
           const double r = sqrt(-2.0 * log(rand_open_unit(b.v[2 * q])));
           double sn, cs;
@@ -1308,7 +1343,7 @@ __global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restri
         for (int k = 0; k <= i; ++k) acc += chol[i * D + k] * z[k];
         dvec[i] = acc / nz;
       }
-      const Philox4 b = philox4x64((uint64_t)t, wid, it, 40ull, key0, key1);
+      const Philox4 b = philox4x64((uint64_t)t, wid, it, 40ull, T.key0, T.key1);
       lo = -rand_open_unit(b.v[0]);
       hi = lo + 1.0;
       jl = (int)floor((double)kHrssMaxOut * rand_open_unit(b.v[1]));
@@ -1316,6 +1351,8 @@ __global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restri
       nsh = 0;
       phase = jl > 0 ? 0 : (kr > 0 ? 1 : 2);
     }
+    __syncthreads();
+    if (s_stop) break;
     // step-out evaluations <= kHrssMaxOut - 1, shrinkage draws <= kHrssMaxShrink
     for (int iter = 0; iter < kHrssMaxOut + kHrssMaxShrink; ++iter) {
       if (threadIdx.x == 0) {
@@ -1324,7 +1361,7 @@ __global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restri
         } else if (phase == 1) {
           tc = hi;
         } else {
-          const Philox4 b = philox4x64((uint64_t)t, wid, it, 48ull + (uint64_t)(nsh >> 2), key0, key1);
+          const Philox4 b = philox4x64((uint64_t)t, wid, it, 48ull + (uint64_t)(nsh >> 2), T.key0, T.key1);
           tc = lo + (hi - lo) * rand_open_unit(b.v[nsh & 3]);
         }
         int inb = 1;
@@ -1335,17 +1372,31 @@ __global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restri
           if (!(v >= 0.0 && v <= 1.0)) inb = 0;
         }
         s_eval = inb;
-        if (inb) setup_from_unit<0, WF>(ev, pt, P);
+        if (inb) setup_from_unit<PREC, WF>(ev, pt, P);
       }
       __syncthreads();
       const int evaluate = s_eval;
-      if (evaluate) cta_sums<0, NDET, WF>(ev, P, red, vals);
+      if (evaluate) {
+        if (rb) {
+          if constexpr (PREC == 2) {
+            if (threadIdx.x < 32) {
+              int kb = 0;
+              const double v = rb_lnl_warp<NDET, WF>(ev, P, threadIdx.x, &kb);
+              if (threadIdx.x == 0) { s_rbl = v; s_rbk = kb; }
+            }
+            __syncthreads();
+          }
+        } else {
+          cta_sums<PREC, NDET, WF>(ev, P, red, vals);
+        }
+      }
       if (threadIdx.x == 0) {
         bool ins = false;
         double l = 0.0;
         if (evaluate) {
-          l = lnl_from_vals<0, NDET, WF>(ev, P, vals);
+          l = rb ? s_rbl : lnl_from_vals<PREC, NDET, WF>(ev, P, vals);
           ++calls;
+          n_bins += rb ? s_rbk : P.k_end;
           ins = l > lnl_star;
         }
         int end = 0;
@@ -1371,11 +1422,13 @@ __global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restri
       if (s_end) break;
     }
   }
-  if ((int)threadIdx.x < D) u_out[(size_t)j * D + threadIdx.x] = x[threadIdx.x];
+  if ((int)threadIdx.x < D) T.u_out[(size_t)j * D + threadIdx.x] = x[threadIdx.x];
   if (threadIdx.x == 0) {
-    lnl_out[j] = lnl;
-    n_move[j] = moves;
-    n_like[j] = calls;
+    T.lnl_out[j] = lnl;
+    T.n_acc[j] = moves;
+    T.n_like[j] = calls;
+    if (T.n_bins) T.n_bins[j] = n_bins;
+    if (T.n_spec) T.n_spec[j] = calls;
   }
 }
 
@@ -1420,6 +1473,15 @@ cudaError_t launch_walk_p(int waveform, int n_det, const EventDev* d_evs, WalkTa
 #define GWNS_WALK(P_, N, W) launch_walk_one<P_, N, W>(n_blocks, s, d_evs, d_tasks, d_blk_task, d_blk_local)
   GWNS_DISPATCH_W(GWNS_WALK, P)
 #undef GWNS_WALK
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_hrss_p(int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
+                          const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s) {
+#define GWNS_HRSS(P_, N, W) hrss_kernel<P_, N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local)
+  GWNS_DISPATCH_W(GWNS_HRSS, P)
+#undef GWNS_HRSS
   return cudaGetLastError();
 }
 

@@ -9,24 +9,13 @@ template cudaError_t launch_unit_likelihood_p<0>(int, int, const EventDev*, cons
                                                   cudaStream_t);
 template cudaError_t launch_walk_p<0>(int, int, const EventDev*, WalkTask*, const int32_t*, const int32_t*, int,
                                        cudaStream_t);
+template cudaError_t launch_hrss_p<0>(int, int, const EventDev*, WalkTask*, const int32_t*, const int32_t*, int,
+                                       cudaStream_t);
 
 cudaError_t launch_unit_to_theta(const EventDev* d_ev, const double* d_u, int64_t n, double* d_theta,
                                  cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   unit_to_theta_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(d_ev, d_u, n, d_theta);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_hrss(int waveform, int n_det, const EventDev* d_ev, const double* d_chol, const double* d_u0,
-                        const double* d_lnl0, double lnl_star, int n, int n_steps, uint64_t iteration,
-                        int64_t walker_offset, uint64_t key0, uint64_t key1, double* d_uo, double* d_lo,
-                        int32_t* d_nm, int32_t* d_nl, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-#define GWNS_HRSS(P_, N, W)                                                                                  \
-  hrss_kernel<N, W><<<n, kThreads, 0, s>>>(d_ev, d_chol, d_u0, d_lnl0, lnl_star, n_steps, iteration,        \
-                                          walker_offset, key0, key1, d_uo, d_lo, d_nm, d_nl)
-  GWNS_DISPATCH_W(GWNS_HRSS, 0)
-#undef GWNS_HRSS
   return cudaGetLastError();
 }
 

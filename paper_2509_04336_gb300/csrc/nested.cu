@@ -247,12 +247,14 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
       S.spec = min(S.spec_rule, S.spec_cap);
     }
     if (n_zero > 0.0) S.zero_accept = 1;
-    // walk-length retune (batch-scaled delay)
-    double ns = (double)S.n_steps;
-    double x = (S.delay_k * ns + ns * (double)S.naccept / fmax(mean_acc, 0.5)) / (S.delay_k + 1.0);
-    double r = floor(x + 0.5);
-    r = fmin(fmax(r, 1.0), (double)S.maxmcmc);
-    S.n_steps = (int32_t)r;
+    // walk-length retune (batch-scaled delay); HRSS keeps its fixed move count
+    if (S.hrss == 0) {
+      double ns = (double)S.n_steps;
+      double x = (S.delay_k * ns + ns * (double)S.naccept / fmax(mean_acc, 0.5)) / (S.delay_k + 1.0);
+      double r = floor(x + 0.5);
+      r = fmin(fmax(r, 1.0), (double)S.maxmcmc);
+      S.n_steps = (int32_t)r;
+    }
     S.iteration += 1;
     S.lnl_max = lmax;
     S.dlogz = logaddexp(S.log_z, lmax + S.log_x) - S.log_z;
@@ -267,6 +269,55 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
     tasks[blockIdx.x].done = S.done;
     tasks[blockIdx.x].n_steps = S.n_steps;
     tasks[blockIdx.x].spec = S.spec;
+  }
+}
+
+// HRSS: the lower Cholesky factor of the survivors' sample covariance (divisor n_s - 1, unit-cube
+// coordinates), one CTA per event, after the deletion: the direction factor of the batch's
+// slice-sampling lines.  A pivot at the rounding level of its variance (the survivors span fewer
+// than D directions) stops the event with chol_bad set.
+__global__ void __launch_bounds__(kSelThreads) chol_kernel(NsState* states, WalkTask* tasks) {
+  __shared__ double mean[kMaxDim];
+  __shared__ double cov[kMaxDim * kMaxDim];
+  NsState& S = states[blockIdx.x];
+  if (S.done || S.hrss == 0) return;
+  const int D = S.D, ns = S.n_live - S.k, tid = threadIdx.x;
+  for (int i = tid; i < D; i += kSelThreads) {
+    double a = 0.0;
+    for (int p = 0; p < ns; ++p) a += S.surv_u[(size_t)p * D + i];
+    mean[i] = a / (double)ns;
+  }
+  __syncthreads();
+  for (int q = tid; q < D * D; q += kSelThreads) {
+    const int i = q / D, k = q % D;
+    if (k > i) continue;
+    double a = 0.0;
+    for (int p = 0; p < ns; ++p)
+      a += (S.surv_u[(size_t)p * D + i] - mean[i]) * (S.surv_u[(size_t)p * D + k] - mean[k]);
+    cov[q] = a / (double)(ns - 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double* L = S.chol;
+    bool ok = true;
+    for (int i = 0; i < D && ok; ++i)
+      for (int k = 0; k <= i; ++k) {
+        double a = cov[i * D + k];
+        for (int m = 0; m < k; ++m) a -= L[i * D + m] * L[k * D + m];
+        if (i == k) {
+          if (!(a > 1e-12 * cov[i * D + i]) || !(a > 0.0)) { ok = false; break; }
+          L[i * D + i] = sqrt(a);
+        } else {
+          L[i * D + k] = a / L[k * D + k];
+        }
+      }
+    for (int i = 0; i < D; ++i)
+      for (int k = i + 1; k < D; ++k) L[i * D + k] = 0.0;
+    if (!ok) {
+      S.chol_bad = 1;
+      S.done = 1;
+      tasks[blockIdx.x].done = 1;
+    }
   }
 }
 
@@ -417,8 +468,15 @@ int enqueue_batch(ns_handle* h, int b, int64_t* launches) {
   // flag makes it an event-record node that timestamps every replay
   if ((e = cudaEventRecordWithFlags(h->walk_events[2 * b], h->stream, cudaEventRecordExternal)) != cudaSuccess)
     return cuda_fail(h, e, "event");
-  e = launch_walk(h->precision, h->waveform, h->max_det, h->d_events, h->d_tasks, h->d_blk_task, h->d_blk_local,
-                  h->n_walk_blocks, h->stream);
+  if (h->hrss) {
+    chol_kernel<<<ne, kSelThreads, 0, h->stream>>>(h->d_ns, h->d_tasks);
+    *launches += 1;
+    e = launch_hrss(h->precision, h->waveform, h->max_det, h->d_events, h->d_tasks, h->d_blk_task, h->d_blk_local,
+                    h->n_walk_blocks, h->stream);
+  } else {
+    e = launch_walk(h->precision, h->waveform, h->max_det, h->d_events, h->d_tasks, h->d_blk_task, h->d_blk_local,
+                    h->n_walk_blocks, h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "walk launch");
   if ((e = cudaEventRecordWithFlags(h->walk_events[2 * b + 1], h->stream, cudaEventRecordExternal)) != cudaSuccess)
     return cuda_fail(h, e, "event");
@@ -483,7 +541,9 @@ int nested_init(ns_handle* h) {
     S.key0 = c.seed;
     S.key1 = (uint64_t)e;
     S.dead_cap = (int64_t)S.k * 64;
-    S.spec_auto = c.spec_depth == 0;
+    S.hrss = c.proposal == NS_PROPOSAL_HRSS ? (c.hrss_moves > 0 ? c.hrss_moves : 2 * E.n_dim) : 0;
+    if (S.hrss) S.n_steps = S.hrss;
+    S.spec_auto = c.spec_depth == 0 && S.hrss == 0;
     S.spec_cap = h->precision == 0 ? 8 : kSpecMax;
     S.spec_rule = 4;
     S.spec = c.spec_depth > 0 ? c.spec_depth : 4;
@@ -506,7 +566,8 @@ int nested_init(ns_handle* h) {
         (r = alloc(h, (void**)&S.dead_u, sizeof(double) * S.dead_cap * D, "dead_u")) ||
         (r = alloc(h, (void**)&S.dead_lnl, sizeof(double) * S.dead_cap, "dead_lnl")) ||
         (r = alloc(h, (void**)&S.dead_logw, sizeof(double) * S.dead_cap, "dead_logw")) ||
-        (r = alloc(h, (void**)&S.dead_nlive, sizeof(int32_t) * S.dead_cap, "dead_nlive")))
+        (r = alloc(h, (void**)&S.dead_nlive, sizeof(int32_t) * S.dead_cap, "dead_nlive")) ||
+        (S.hrss && (r = alloc(h, (void**)&S.chol, sizeof(double) * D * D, "chol"))))
       return r;
     WalkTask& T = tasks[e];
     std::memset(&T, 0, sizeof(T));
@@ -515,6 +576,8 @@ int nested_init(ns_handle* h) {
     T.lnl_star = -INFINITY; T.iteration = 0; T.walker_offset = 0;
     T.key0 = S.key0; T.key1 = S.key1; T.n_s = S.n_live - S.k; T.n = S.k; T.n_steps = S.n_steps;
     T.done = 0; T.event = e;
+    T.chol = S.chol;
+    watchdog_fields(h, T);
     flow_task_fields(E, T);
     total_walkers += S.k;
   }
@@ -554,7 +617,7 @@ void nested_free(ns_handle* h) {
   for (auto& E : h->events) {
     NsState& S = E.ns;
     void* ptrs[] = {S.live_u, S.live_lnl, S.surv_u, S.survf, S.w_u0, S.w_lnl0, S.w_uo, S.w_lo, S.w_na, S.w_nl,
-                    S.slot, S.w_nb, S.w_ns, S.dead_u, S.dead_lnl, S.dead_logw, S.dead_nlive};
+                    S.slot, S.w_nb, S.w_ns, S.dead_u, S.dead_lnl, S.dead_logw, S.dead_nlive, S.chol};
     for (void* p : ptrs) cudaFree(p);
     std::memset(&S, 0, sizeof(S));
   }
@@ -622,6 +685,10 @@ extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
   for (auto& S : h->host_ns) all_done = all_done && S.done;
   int left = all_done ? 0 : max_batches;
   const int G = 8;
+  {
+    cudaError_t e = cudaMemsetAsync(h->d_status + 2, 0, sizeof(int32_t), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "watchdog reset");
+  }
   bool all_auto = true;
   for (auto& E : h->events) all_auto = all_auto && E.ns.spec_auto;
   h->tune = all_auto;
@@ -701,6 +768,10 @@ extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
   if (progress) fill_progress(h, progress);
   for (auto& S : h->host_ns)
     if (S.overflow) return set_error(h, NS_ENOMEM, "dead-point store overflow");
+  for (size_t e = 0; e < h->host_ns.size(); ++e)
+    if (h->host_ns[e].chol_bad)
+      return set_error(h, NS_EINVAL, "event %zu: the survivors' covariance is not positive definite (HRSS)", e);
+  if ((r = watchdog_report(h))) return r;
   bool warn = false;
   for (auto& S : h->host_ns) warn = warn || S.zero_accept;
   return warn ? NS_WMAXMCMC : NS_OK;

@@ -108,9 +108,11 @@ extern "C" int ns_walk_batch_noalloc(ns_handle* h, int event, const double* live
   T.done = 0;
   T.event = event;
   T.spec = E.cfg.spec_depth > 0 ? E.cfg.spec_depth : default_spec(h->precision);
+  watchdog_fields(h, T);
   cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
-  // the flow kernels' timeout flag starts clear, as in ns_walk_batch
-  if ((e = cudaMemsetAsync(h->d_status + 1, 0, sizeof(int32_t), s)) != cudaSuccess) return cuda_fail(h, e, "status reset");
+  // the flow kernels' timeout flag and the walk watchdog's bit start clear, as in ns_walk_batch
+  if ((e = cudaMemsetAsync(h->d_status + 1, 0, sizeof(int32_t) * 2, s)) != cudaSuccess)
+    return cuda_fail(h, e, "status reset");
   // flow steps draw on the handle's own proposal table, allocated at ns_init
   r = flow_attach(h, event, T, n, n_steps, nullptr, s);
   if (r) return r;

@@ -25,7 +25,7 @@ NS_OK, NS_EINVAL, NS_ECUDA, NS_ENOMEM, NS_ENONFINITE, NS_ETIMEOUT, NS_ESTATE, NS
 NS_WMAXMCMC = 1
 NS_PTR_HOST, NS_PTR_DEVICE = 0, 1
 NS_PREC_FP64, NS_PREC_MIXED, NS_PREC_MIXED_FF = 0, 1, 2
-NS_PROPOSAL_DE, NS_PROPOSAL_DE_FLOW = 0, 1
+NS_PROPOSAL_DE, NS_PROPOSAL_DE_FLOW, NS_PROPOSAL_HRSS = 0, 1, 2
 STATUS_NAMES = {0: "NS_OK", -1: "NS_EINVAL", -2: "NS_ECUDA", -3: "NS_ENOMEM", -4: "NS_ENONFINITE",
                 -5: "NS_ETIMEOUT", -6: "NS_ESTATE", -7: "NS_EIO", 1: "NS_WMAXMCMC"}
 
@@ -42,7 +42,7 @@ class ns_config(C.Structure):
                 ("precision", C.c_int32), ("waveform", C.c_int32), ("max_iter", C.c_int32),
                 ("n_steps0", C.c_int32), ("seed", C.c_uint64), ("spec_depth", C.c_int32), ("proposal", C.c_int32),
                 ("p_flow", C.c_double), ("flow_layers", C.c_int32), ("flow_every", C.c_int32),
-                ("flow_epochs", C.c_int32), ("reserved", C.c_int32), ("flow_lr", C.c_double)]
+                ("flow_epochs", C.c_int32), ("hrss_moves", C.c_int32), ("flow_lr", C.c_double)]
 
 
 class ns_detector(C.Structure):
@@ -69,7 +69,8 @@ class ns_progress(C.Structure):
 EXPORTS = ("ns_init", "ns_waveform", "ns_likelihood_batch", "ns_walk_batch", "ns_step", "ns_evidence",
            "ns_posterior", "ns_state_save", "ns_state_load", "ns_walk_batch_noalloc", "ns_flow_num_params",
            "ns_flow_set", "ns_flow_get", "ns_flow_logq", "ns_flow_sample", "ns_flow_grad", "ns_flow_train",
-           "ns_relbin_set", "ns_relbin_edges", "ns_hrss_batch", "ns_free", "ns_last_error")
+           "ns_relbin_set", "ns_relbin_edges", "ns_hrss_batch", "ns_set_watchdog", "ns_set_abort", "ns_free",
+           "ns_last_error")
 
 _lib = None
 
@@ -104,6 +105,8 @@ def load(path: str = LIB_PATH):
     lib.ns_relbin_set.argtypes = [P, I, P, I, P]
     lib.ns_relbin_edges.argtypes = [D, D, I, D, P, I, C.POINTER(C.c_int32)]
     lib.ns_hrss_batch.argtypes = [P, I, P, I, P, P, D, I, I, C.c_int64, C.c_int64, P, P, P, P]
+    lib.ns_set_watchdog.argtypes = [P, D]
+    lib.ns_set_abort.argtypes = [P, I]
     lib.ns_free.argtypes = [P]
     lib.ns_free.restype = None
     lib.ns_last_error.argtypes = [P]
@@ -165,8 +168,9 @@ def _same_kind(*arrays):
 # ---------------------------------------------------------------- marshalling helpers
 def make_config(w: synth.Workload, priors=None, *, precision=None, max_iter=0, n_steps0=0, delay=-1.0,
                 seed=None, spec_depth=0, p_flow=None, flow_layers=0, flow_every=0, flow_epochs=0,
-                flow_lr=0.0) -> ns_config:
-    """ns_config of a workload; p_flow (not None) selects NS_PROPOSAL_DE_FLOW."""
+                flow_lr=0.0, hrss_moves=None) -> ns_config:
+    """ns_config of a workload; p_flow (not None) selects NS_PROPOSAL_DE_FLOW, hrss_moves (not
+    None; 0 means 2 D) NS_PROPOSAL_HRSS."""
     c = ns_config()
     pri = w.priors if priors is None else priors
     for i, p in enumerate(pri):
@@ -184,6 +188,9 @@ def make_config(w: synth.Workload, priors=None, *, precision=None, max_iter=0, n
         c.proposal = NS_PROPOSAL_DE_FLOW
         c.p_flow = p_flow
         c.flow_layers, c.flow_every, c.flow_epochs, c.flow_lr = flow_layers, flow_every, flow_epochs, flow_lr
+    if hrss_moves is not None:
+        c.proposal = NS_PROPOSAL_HRSS
+        c.hrss_moves = hrss_moves
     return c
 
 
@@ -382,6 +389,14 @@ def ns_hrss_batch(h, event: int, live_u, u0, lnl0, lnl_star: float, n_steps: int
                               float(lnl_star), n, n_steps, iteration, walker_offset, uo.ctypes.data,
                               lo.ctypes.data, nm.ctypes.data, nl.ctypes.data), h)
     return uo, lo, nm, nl
+
+
+def ns_set_watchdog(h, budget_seconds: float):
+    return _check(_lib.ns_set_watchdog(h, float(budget_seconds)), h)
+
+
+def ns_set_abort(h, flag: bool):
+    return _check(_lib.ns_set_abort(h, 1 if flag else 0), h)
 
 
 def ns_free(h):

@@ -85,7 +85,8 @@ def _event_and_config():
     (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_DE_FLOW), setattr(c, "p_flow", 1.5)), gwns.NS_EINVAL),
     (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_DE_FLOW), setattr(c, "flow_layers", 17)), gwns.NS_EINVAL),
     (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_DE_FLOW), setattr(c, "flow_lr", -1.0)), gwns.NS_EINVAL),
-    (lambda c, e: setattr(c, "reserved", 1), gwns.NS_EINVAL),
+    (lambda c, e: setattr(c, "hrss_moves", 1), gwns.NS_EINVAL),            # HRSS moves without HRSS
+    (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_HRSS), setattr(c, "hrss_moves", -1)), gwns.NS_EINVAL),
 ])
 def test_init_rejects_bad_input_without_device_work(lib, mutate, code):
     w, ev = _event_and_config()
