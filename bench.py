@@ -120,6 +120,8 @@ def build_events(name: str, rank: int, device: int):
 
 
 WORKLOAD_DESCRIPTIONS = {
+    "four_param_2det_taylorf2": "four_param_2det_taylorf2: 2 detectors, 1969 bins (4 s, 20-512 Hz), TaylorF2, 4 params "
+                                "(Mc, q, chi1, chi2), n_live 100, num_delete 50, naccept 20, SNR 20, zero noise",
     "bbh11_3det_4s_taylorf2": "bbh11_3det_4s_taylorf2: 3 detectors, 4017 bins (4 s, 20-1024 Hz), TaylorF2, 11 params, "
                               "n_live 1000, num_delete 500, naccept 60, SNR 39.6, seeded noise",
     "bbh11_3det_8s_phenomd": "bbh11_3det_8s_phenomd: 3 detectors, 16,225 bins (8 s, 20-2048 Hz), IMRPhenomD form, "
@@ -684,6 +686,120 @@ def run_logz_seeds(args):
     return 0
 
 
+def run_hrss(args):
+    """HRSS line: the sampler with hit-and-run slice sampling as its inner kernel against the DE
+    walk on --workload, both in the float-float mode: lnL evals/s over K batches after W warm-up
+    batches (L2 flushed between them), then each run from ns_init to its stopping rule (wall time
+    to ln Z, likelihood calls per effective posterior sample)."""
+    import torch
+
+    from paper_2509_04336_gb300 import build, gwns
+
+    rank, world, local = rank_info()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    build.build()
+    gwns.load()
+    w, ev = library_event(synth.workload(args.workload), 0, local)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    arms = {}
+    kinds = (("de", {}), ("hrss", {"hrss_moves": args.hrss_moves}))
+    with ClockSampler(local) as clocks:
+        for tag, kw in kinds:
+            h = gwns.ns_init([gwns.make_config(w, synth.priors_with_injection(w, ev), precision=synth.PREC_MIXED_FF,
+                                               **kw)], [ev], local)
+            try:
+                for _ in range(args.warmup):
+                    gwns.ns_step(h, 1)
+                _, p0 = gwns.ns_step(h, 0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ms = 0.0
+                for _ in range(args.steps):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    e0.record()
+                    _, p = gwns.ns_step(h, 1)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                evals = p[0]["n_like"] - p0[0]["n_like"]
+                arms[tag] = {"lnl_evals_per_s": evals / (ms * 1e-3), "ms_per_step": ms / args.steps,
+                             "walk_ms_per_step": (p[0]["walk_ms"] - p0[0]["walk_ms"]) / args.steps,
+                             "steps_per_walker": p[0]["n_steps"], "mean_accept": p[0]["mean_accept"],
+                             "lnl_calls_per_walker_batch": evals / args.steps / w.num_delete}
+            finally:
+                gwns.ns_free(h)
+    for tag, kw in kinds:
+        arms[tag]["to_logz"] = run_to_logz(gwns, w, ev, synth.PREC_MIXED_FF, local, **kw)
+    ck = clocks.summary()
+    de, hr = arms["de"]["to_logz"], arms["hrss"]["to_logz"]
+    line = {
+        "metric": "HRSS inner kernel: wall time to ln Z and lnL calls per effective sample against the DE walk",
+        "value": hr["seconds"], "unit": "s to ln Z", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESCRIPTIONS[args.workload], "precision": "float-float phase (mode 2)",
+                   "hrss_moves": args.hrss_moves or 2 * w.n_dim, "l2": "flushed (256 MB write) between timed steps"},
+        "de": arms["de"], "hrss": arms["hrss"],
+        "time_to_logz_ratio_hrss_over_de": hr["seconds"] / de["seconds"],
+        "lnl_calls_per_ess_ratio_hrss_over_de": hr["lnl_evals_per_ess"] / de["lnl_evals_per_ess"],
+        "delta_log_z": hr["log_z"] - de["log_z"],
+        "combined_log_z_err": math.hypot(hr["log_z_err"], de["log_z_err"]),
+        "clocks": {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons", [])},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_logz_convergence(args):
+    """ln Z of the headline configuration against the inner kernel's decorrelation: the DE walk
+    with naccept and maxmcmc scaled up, and HRSS with more moves a batch, each on N seeds (noise
+    realisation and sampler seed), float-float mode; mean ln Z and its standard error per arm, and
+    every run's ln Z minus the same seed's reference arm (DE, naccept 60, maxmcmc 5000)."""
+    import torch
+
+    from dataclasses import replace
+
+    from paper_2509_04336_gb300 import build, gwns
+
+    rank, world, local = rank_info()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    build.build()
+    gwns.load()
+    base = synth.workload(args.workload)
+    arms = [("de_60_5000", {}, {}), ("de_120_20000", {"naccept": 120, "maxmcmc": 20000}, {}),
+            ("de_240_50000", {"naccept": 240, "maxmcmc": 50000}, {}),
+            ("hrss_22", {}, {"hrss_moves": 22}), ("hrss_66", {}, {"hrss_moves": 66}),
+            ("hrss_198", {}, {"hrss_moves": 198})]
+    out = {a[0]: [] for a in arms}
+    for sd in range(args.logz_seeds):
+        w0, ev = library_event(base, sd, local)
+        w0 = replace(w0, seed=base.seed + sd)
+        for tag, wk, ck in arms:
+            r = run_to_logz(gwns, replace(w0, **wk), ev, synth.PREC_MIXED_FF, local, **ck)
+            out[tag].append(r)
+            print(json.dumps({"seed": sd, "arm": tag, "log_z": r["log_z"], "log_z_err": r["log_z_err"],
+                              "seconds": r["seconds"], "n_like": r["n_like"], "iterations": r["iterations"]}),
+                  file=sys.stderr, flush=True)
+    ref = np.array([r["log_z"] for r in out["de_60_5000"]])
+    summary = {}
+    for tag, _, _ in arms:
+        lz = np.array([r["log_z"] for r in out[tag]])
+        d = lz - ref
+        n = lz.size
+        summary[tag] = {"mean_log_z": float(lz.mean()), "mean_delta_vs_de_60_5000": float(d.mean()),
+                        "stderr_delta": float(d.std(ddof=1) / math.sqrt(n)) if n > 1 else None,
+                        "mean_log_z_err": float(np.mean([r["log_z_err"] for r in out[tag]])),
+                        "mean_seconds": float(np.mean([r["seconds"] for r in out[tag]])),
+                        "mean_n_like": float(np.mean([r["n_like"] for r in out[tag]])),
+                        "mean_lnl_evals_per_ess": float(np.mean([r["lnl_evals_per_ess"] for r in out[tag]]))}
+    print(json.dumps({"metric": "ln Z against the inner kernel's decorrelation (float-float mode)",
+                      "workload": WORKLOAD_DESCRIPTIONS[args.workload], "seeds": args.logz_seeds, "arms": summary}))
+    return 0
+
+
 def run_profile_case(args):
     """A small case for profilers: N batches of the bench workload, no timing."""
     from paper_2509_04336_gb300 import build, gwns
@@ -693,6 +809,8 @@ def run_profile_case(args):
     torch.cuda.set_device(0)
     ws, evs = build_events(args.workload, 0, 0)
     kw = {"p_flow": args.p_flow, "flow_layers": 8} if args.workload.endswith("_flow") else {}
+    if args.hrss:
+        kw["hrss_moves"] = args.hrss_moves
     cfgs = [gwns.make_config(w, synth.priors_with_injection(w, e), precision=args.precision, **kw)
             for w, e in zip(ws, evs)]
     h = gwns.ns_init(cfgs, evs)
@@ -815,19 +933,28 @@ def main():
     ap.add_argument("--relbin", type=float, default=0.0,
                     help="eps [rad] > 0: the relative-binning line (full vs relative-binning likelihood) "
                          "on --workload instead of the headline line")
+    ap.add_argument("--hrss", action="store_true",
+                    help="the HRSS line (slice-sampling inner kernel against the DE walk) on --workload instead")
+    ap.add_argument("--hrss-moves", type=int, default=0, help="HRSS moves per walker and batch (0: 2 D)")
+    ap.add_argument("--logz-convergence", action="store_true",
+                    help="with --logz-seeds N: ln Z of DE walks with longer walks and of HRSS with more moves")
     ap.add_argument("--logz-seeds", type=int, default=0,
                     help="N > 0: run --workload to ln Z in float-float and plain FP64 on N seeds instead")
     args = ap.parse_args()
+    if args.profile_batches > 0:
+        return run_profile_case(args)
     if args.logz_seeds > 0:
-        return run_logz_seeds(args)
+        return run_logz_convergence(args) if args.logz_convergence else run_logz_seeds(args)
+    if args.hrss:
+        if args.workload == "batched64" or args.workload.endswith("_flow"):
+            ap.error("--hrss runs a single-event DE workload")
+        return run_hrss(args)
     if args.relbin > 0.0:
         if args.workload == "batched64":
             ap.error("--relbin runs a single-event workload")
         if args.warmup < 3:
             ap.error("--warmup must be >= 3")
         return run_relbin(args)
-    if args.profile_batches > 0:
-        return run_profile_case(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
