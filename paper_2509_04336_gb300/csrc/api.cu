@@ -380,6 +380,11 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
 // Speculation depth of a stand-alone walk when the configuration leaves it automatic.
 int default_spec(int precision) { return precision == NS_PREC_FP64 ? 4 : 16; }
 
+// Candidates per round of the float-float HRSS kernel when the configuration leaves it automatic:
+// TaylorF2 evaluates a warp per candidate (8: two rounds of the four warps cost about one), the
+// IMRPhenomD form runs each candidate on the whole CTA (2).
+int hrss_default_spec(int waveform) { return waveform == NS_WAVEFORM_TAYLORF2 ? 8 : 2; }
+
 static cudaStream_t pick_stream(ns_handle* h, void* stream) {
   return stream ? (cudaStream_t)stream : h->stream;
 }

@@ -115,6 +115,7 @@ int cuda_fail(ns_handle* h, cudaError_t e, const char* what);
 int ensure_scratch(ns_handle* h, gwns::Scratch& s, size_t bytes);
 int nested_init(ns_handle* h);
 int default_spec(int precision);
+int hrss_default_spec(int waveform);
 void nested_free(ns_handle* h);
 void relbin_free(gwns::EventHost& E);
 // flow proposal (flow_api.cu)

@@ -70,7 +70,7 @@ extern "C" int ns_hrss_batch(ns_handle* h, int event, const double* live_u, int 
   T.n = n;
   T.n_steps = n_steps;
   T.event = event;
-  T.spec = 1;
+  T.spec = E.cfg.spec_depth > 0 ? E.cfg.spec_depth : hrss_default_spec(h->waveform);
   watchdog_fields(h, T);
   const size_t task_b = (sizeof(WalkTask) + 255) / 256 * 256;
   const size_t maps_b = (2 * sizeof(int32_t) * (size_t)n + 255) / 256 * 256;

@@ -1432,6 +1432,333 @@ __global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restri
   }
 }
 
+// ---------------------------------------------------------------- speculative HRSS (mode 2)
+// The slice-sampling moves of hrss_kernel, with the candidate evaluations of a move batched into
+// rounds that run like the float-float walk's: the candidates' points in FP64 on warp 0 (one lane
+// each), their constants on the setup warps, their likelihoods one warp per candidate (TaylorF2,
+// relative binning) or on the whole CTA in turn (IMRPhenomD form), then thread 0 replays the
+// sequential slice logic over them in order.  Which candidates the sequential move evaluates
+// next depends on outcomes only through where it stops:
+//   stepping out: the left end is tried at lo, lo - 1, lo - 2, ... while it is inside the slice
+//     (budget J) and the right end at hi, hi + 1, ... (budget K); a round holds the next ends of
+//     both sides, as if every one were inside, and the replay stops each side at its first end
+//     outside the slice (the two sides do not interact, so their order does not matter);
+//   shrinkage: with the draws U_j fixed by their Philox counters, the j-th candidate is
+//     t_j = lo_j + (hi_j - lo_j) U_j, where (lo_j, hi_j) is the bracket left by rejecting
+//     t_1 .. t_{j-1}; a round holds the next candidates as if all were rejected, and the replay
+//     takes the first inside the slice.
+// The chain, the moves and the likelihood-call counts are those of the one-candidate kernel (calls
+// of candidates after the replay's stopping point are counted in n_spec only); per round at most
+// task.spec candidates (1 .. kHrssQ).  Directions: warp 0's lanes draw the normals (Box-Muller on
+// the Philox blocks of hrss_kernel) and form d = C z / |z| row by row in the same order.
+constexpr int kHrssQ = 16;
+
+template <int NDET, int WF>
+__global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __restrict__ evs, WalkTask* tasks,
+                                                             const int32_t* __restrict__ blk_task,
+                                                             const int32_t* __restrict__ blk_local) {
+  constexpr int NV = NVals<NDET, WF>::value;
+  __shared__ WalkerParams P[kHrssQ];
+  __shared__ ff propf[kHrssQ][kMaxDim];
+  __shared__ TF2Part parts[WF == 0 ? kHrssQ : 1];
+  __shared__ float part_sums[kHrssQ][2 * kMaxVals];
+  __shared__ float wsums[WF == 1 ? kHrssQ : 1][kWarps][2 * kMaxVals];
+  __shared__ double s_rbl[kHrssQ];
+  __shared__ int s_rbk[kHrssQ];
+  __shared__ double x[kMaxDim], dvec[kMaxDim], zn[kMaxDim + 1];
+  __shared__ double ct[kHrssQ];              // t of each candidate of the round, in evaluation order
+  __shared__ double cpt[kHrssQ][kMaxDim];    // its point
+  __shared__ int cslot[kHrssQ];              // its likelihood slot, -1 for a point outside the cube
+  __shared__ double lnl_c[kHrssQ];           // ln L of each slot
+  __shared__ int kend_c[kHrssQ];             // grid bins each slot's evaluation touched
+  __shared__ int s_nc, s_nin, s_newmove, s_exit, s_t;
+  const WalkTask& T = tasks[blk_task[blockIdx.x]];
+  const int j = blk_local[blockIdx.x];
+  const EventDev& ev = evs[T.event];
+  if (T.done) return;
+  const int D = ev.n_dim;
+  const int n_steps = T.n_steps;
+  const double lnl_star = T.lnl_star;
+  const uint64_t it = (uint64_t)T.iteration;
+  const uint64_t wid = (uint64_t)(T.walker_offset + j);
+  const double* chol = T.chol;
+  const int Q = T.spec < 1 ? 1 : (T.spec > kHrssQ ? kHrssQ : T.spec);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool split = WF == 0 && ev.ff_setup;
+  const bool rb = ev.rb_nb > 0;
+  const int sw = (int)(blockIdx.x % (unsigned)kWarps);   // the setup warp of the non-split setups
+  if ((int)threadIdx.x < D) x[threadIdx.x] = T.u0[(size_t)j * D + threadIdx.x];
+  double lnl = T.lnl0[j];
+  int moves = 0, calls = 0;
+  int64_t n_bins = 0, n_spec = 0;
+  const uint64_t t0 = threadIdx.x == 0 ? global_ns() : 0ull;
+  // thread 0's move state: t the move, stepping (the bracket's ends still extend: jl, kr left),
+  // lo, hi the bracket, nsh shrinkage draws used
+  int t = 0, jl = 0, kr = 0, nsh = 0;
+  bool left_on = false, right_on = false;
+  double lo = 0.0, hi = 0.0;
+  if (threadIdx.x == 0) {
+    s_exit = n_steps <= 0 ? 1 : 0;
+    s_newmove = 1;
+    s_t = 0;
+  }
+  __syncthreads();
+  while (!s_exit) {
+    // A. warp 0: a new move's direction and bracket when the last move ended; the round's
+    //    candidates and their points
+    if (warp == 0) {
+      if (s_newmove) {
+        if (lane < (D + 3) / 4) {
+          const Philox4 b = philox4x64((uint64_t)s_t, wid, it, 32ull + (uint64_t)lane, T.key0, T.key1);
+          for (int q = 0; q < 2; ++q) {
+            const double r = sqrt(-2.0 * log(rand_open_unit(b.v[2 * q])));
+            double sn, cs;
+            sincospi(2.0 * rand_open_unit(b.v[2 * q + 1]), &sn, &cs);
+            const int i0 = 4 * lane + 2 * q;
+            if (i0 < D) zn[i0] = r * cs;
+            if (i0 + 1 < D) zn[i0 + 1] = r * sn;
+          }
+        }
+        __syncwarp();
+        if (lane < D) {
+          double nz = 0.0;
+          for (int i = 0; i < D; ++i) nz += zn[i] * zn[i];
+          nz = sqrt(nz);
+          double acc = 0.0;
+          for (int k = 0; k <= lane; ++k) acc += chol[lane * D + k] * zn[k];
+          dvec[lane] = acc / nz;
+        }
+        __syncwarp();
+      }
+      if (lane == 0) {
+        if (s_newmove) {
+          const Philox4 b = philox4x64((uint64_t)t, wid, it, 40ull, T.key0, T.key1);
+          lo = -rand_open_unit(b.v[0]);
+          hi = lo + 1.0;
+          jl = (int)floor((double)kHrssMaxOut * rand_open_unit(b.v[1]));
+          kr = kHrssMaxOut - 1 - jl;
+          nsh = 0;
+          left_on = jl > 0;
+          right_on = kr > 0;
+        }
+        int nc = 0;
+        if (left_on || right_on) {
+          // the next ends of both sides, as if every one were inside the slice
+          int ql = left_on ? min(jl, Q) : 0;
+          int qr = right_on ? min(kr, Q) : 0;
+          if (ql + qr > Q) {
+            ql = min(ql, max(Q / 2, Q - qr));
+            qr = min(qr, Q - ql);
+          }
+          for (int i = 0; i < ql; ++i) ct[nc++] = lo - (double)i;
+          for (int i = 0; i < qr; ++i) ct[nc++] = hi + (double)i;
+          s_nc = nc | (ql << 8);
+        } else {
+          // the next shrinkage candidates, as if every one were rejected
+          const int S = min(Q, kHrssMaxShrink - nsh);
+          double l2 = lo, h2 = hi;
+          for (int q = 0; q < S; ++q) {
+            const int jj = nsh + q;
+            const Philox4 b = philox4x64((uint64_t)t, wid, it, 48ull + (uint64_t)(jj >> 2), T.key0, T.key1);
+            const double tc = l2 + (h2 - l2) * rand_open_unit(b.v[jj & 3]);
+            ct[nc++] = tc;
+            if (tc < 0.0) l2 = tc;
+            else h2 = tc;
+          }
+          s_nc = nc;
+        }
+      }
+      __syncwarp();
+      const int nc = s_nc & 255;
+      int inb = 0;
+      if (lane < nc) {
+        const double tc = ct[lane];
+        inb = 1;
+        for (int i = 0; i < D; ++i) {
+          double v = x[i] + tc * dvec[i];
+          if (ev.prior[ev.dim_param[i]].periodic) v -= floor(v);
+          cpt[lane][i] = v;
+          if (!(v >= 0.0 && v <= 1.0)) inb = 0;
+        }
+      }
+      const unsigned im = __ballot_sync(0xffffffffu, inb);
+      const int slot = __popc(im & ((1u << lane) - 1u));
+      if (lane < nc) {
+        cslot[lane] = inb ? slot : -1;
+        if (inb) {
+#pragma unroll
+          for (int d = 0; d < kMaxDim; ++d) propf[slot][d] = d < D ? ff_from_double(cpt[lane][d]) : ff_make(0.0f);
+        }
+      }
+      if (lane == 0) s_nin = __popc(im);
+    }
+    __syncthreads();
+    const int nin = s_nin;
+    // B. the candidates' constants
+    if (nin > 0) {
+      if (split) {
+        if (lane < nin) tf2_split_first(warp, ev, propf[lane], parts[lane], P[lane]);
+        __syncthreads();
+        if (lane < nin) tf2_split_second(warp, ev, parts[lane], P[lane]);
+      } else if (warp == sw && lane < nin) {
+        if (ev.ff_setup) {
+          if (WF == 0) taylorf2_setup_ff(ev, propf[lane], P[lane]);
+          else phenomd_setup_ff(ev, propf[lane], P[lane]);
+        } else {
+          double pd[kMaxDim];
+#pragma unroll
+          for (int d = 0; d < kMaxDim; ++d) pd[d] = d < D ? (double)propf[lane][d].h + (double)propf[lane][d].l : 0.0;
+          setup_from_unit<2, WF>(ev, pd, P[lane]);
+        }
+      }
+      __syncthreads();
+    }
+    // C. likelihoods
+    constexpr int V = Pow2Vals<NV>::value;
+    constexpr int group = 32 / V;
+    if (nin > 0) {
+      if (rb) {
+        for (int i = warp; i < nin; i += kWarps) {
+          int nk;
+          const double v = rb_lnl_warp<NDET, WF>(ev, P[i], lane, &nk);
+          if (lane == 0) { s_rbl[i] = v; s_rbk[i] = nk; }
+        }
+      } else if (WF == 1) {
+        for (int i = 0; i < nin; ++i) {
+          double dv[NV];
+          float fv[NV], fc[NV];
+          partials<2, NDET, WF>(ev, P[i], threadIdx.x, kThreads, dv, fv, fc);
+          float rs, rc;
+          int q;
+          warp_halving_sums<NV>(fv, fc, lane, rs, rc, q);
+          if ((lane & (group - 1)) == 0 && q < NV) { wsums[i][warp][2 * q] = rs; wsums[i][warp][2 * q + 1] = rc; }
+        }
+      } else {
+        for (int i = warp; i < nin; i += kWarps) {
+          double dv[NV];
+          float fv[NV], fc[NV];
+          partials<2, NDET, WF>(ev, P[i], lane, 32, dv, fv, fc);
+          float rs, rc;
+          int q;
+          warp_halving_sums<NV>(fv, fc, lane, rs, rc, q);
+          if ((lane & (group - 1)) == 0 && q < NV) { part_sums[i][2 * q] = rs; part_sums[i][2 * q + 1] = rc; }
+        }
+      }
+      __syncthreads();
+    }
+    // D. ln L of every slot (warp 0), then thread 0 replays the sequential move over the candidates
+    if (warp == 0) {
+      if (lane < nin) {
+        double l;
+        int kb;
+        if (rb) {
+          l = s_rbl[lane];
+          kb = s_rbk[lane];
+        } else if (WF == 1) {
+          float ps[2 * NV];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            float sh = wsums[lane][0][2 * q], sl = wsums[lane][0][2 * q + 1];
+#pragma unroll
+            for (int w2 = 1; w2 < kWarps; ++w2) {
+              float tt, e;
+              two_sum(sh, wsums[lane][w2][2 * q], tt, e);
+              sh = tt;
+              sl += wsums[lane][w2][2 * q + 1] + e;
+            }
+            ps[2 * q] = sh;
+            ps[2 * q + 1] = sl;
+          }
+          l = lnl_ff<NDET, WF>(ev, P[lane], ps);
+          kb = P[lane].k_end;
+        } else {
+          l = lnl_ff<NDET, WF>(ev, P[lane], part_sums[lane]);
+          kb = P[lane].k_end;
+        }
+        lnl_c[lane] = l;
+        kend_c[lane] = kb;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        const int nc = s_nc & 255;
+        n_spec += nin;
+        bool move_end = false;
+        if (left_on || right_on) {
+          const int ql = s_nc >> 8;
+          for (int i = 0; i < ql && left_on; ++i) {
+            const int sl = cslot[i];
+            bool ins = false;
+            if (sl >= 0) {
+              ++calls;
+              n_bins += kend_c[sl];
+              ins = lnl_c[sl] > lnl_star;
+            }
+            if (ins) {
+              lo -= 1.0;
+              if (--jl == 0) left_on = false;
+            } else {
+              left_on = false;
+            }
+          }
+          for (int i = ql; i < nc && right_on; ++i) {
+            const int sl = cslot[i];
+            bool ins = false;
+            if (sl >= 0) {
+              ++calls;
+              n_bins += kend_c[sl];
+              ins = lnl_c[sl] > lnl_star;
+            }
+            if (ins) {
+              hi += 1.0;
+              if (--kr == 0) right_on = false;
+            } else {
+              right_on = false;
+            }
+          }
+        } else {
+          for (int i = 0; i < nc; ++i) {
+            const int sl = cslot[i];
+            if (sl >= 0) {
+              ++calls;
+              n_bins += kend_c[sl];
+              if (lnl_c[sl] > lnl_star) {
+                for (int d = 0; d < D; ++d) x[d] = cpt[i][d];
+                lnl = lnl_c[sl];
+                ++moves;
+                move_end = true;
+                break;
+              }
+            }
+            if (ct[i] < 0.0) lo = ct[i];
+            else hi = ct[i];
+            if (++nsh == kHrssMaxShrink) {
+              move_end = true;
+              break;
+            }
+          }
+        }
+        if (move_end) ++t;
+        s_newmove = move_end ? 1 : 0;
+        s_t = t;
+        if (t >= n_steps) s_exit = 1;
+        if (!s_exit && walk_should_stop(T, t0)) {   // watchdog: the walker stays where it is
+          s_exit = 1;
+          if (T.status) atomicOr(T.status, 1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if ((int)threadIdx.x < D) T.u_out[(size_t)j * D + threadIdx.x] = x[threadIdx.x];
+  if (threadIdx.x == 0) {
+    T.lnl_out[j] = lnl;
+    T.n_acc[j] = moves;
+    T.n_like[j] = calls;
+    if (T.n_bins) T.n_bins[j] = n_bins;
+    if (T.n_spec) T.n_spec[j] = n_spec;
+  }
+}
+
 }  // namespace
 
 // Launchers of one precision P; each kernels_pP.cu instantiates its own.
@@ -1476,10 +1803,18 @@ cudaError_t launch_walk_p(int waveform, int n_det, const EventDev* d_evs, WalkTa
   return cudaGetLastError();
 }
 
+// Mode 2 runs the speculative float-float HRSS kernel; modes 0 and 1 one candidate at a time.
+template <int P, int N, int W>
+void launch_hrss_one(int n_blocks, cudaStream_t s, const EventDev* d_evs, WalkTask* d_tasks,
+                     const int32_t* d_blk_task, const int32_t* d_blk_local) {
+  if constexpr (P == 2) hrss_kernel_ff<N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local);
+  else hrss_kernel<P, N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local);
+}
+
 template <int P>
 cudaError_t launch_hrss_p(int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
                           const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s) {
-#define GWNS_HRSS(P_, N, W) hrss_kernel<P_, N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local)
+#define GWNS_HRSS(P_, N, W) launch_hrss_one<P_, N, W>(n_blocks, s, d_evs, d_tasks, d_blk_task, d_blk_local)
   GWNS_DISPATCH_W(GWNS_HRSS, P)
 #undef GWNS_HRSS
   return cudaGetLastError();

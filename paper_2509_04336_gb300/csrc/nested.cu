@@ -546,7 +546,7 @@ int nested_init(ns_handle* h) {
     S.spec_auto = c.spec_depth == 0 && S.hrss == 0;
     S.spec_cap = h->precision == 0 ? 8 : kSpecMax;
     S.spec_rule = 4;
-    S.spec = c.spec_depth > 0 ? c.spec_depth : 4;
+    S.spec = c.spec_depth > 0 ? c.spec_depth : (S.hrss ? hrss_default_spec(c.waveform) : 4);
     S.spec_mult = 1.4;
     S.spec_p = 0.0;
     const size_t n = S.n_live, k = S.k, D = S.D;

@@ -66,6 +66,27 @@ def test_hrss_chain_mixed_precision(precision):
     assert np.all(gl > lnl_star)
 
 
+@pytest.mark.parametrize("name", ["bbh11_3det_4s_taylorf2", "bbh11_3det_8s_phenomd"])
+def test_hrss_float_float_rounds_give_the_same_chain(name):
+    # the float-float HRSS kernel evaluates up to spec candidates of a move per round and replays
+    # the sequential move over them: any round size gives the same chain, bit for bit (the calls
+    # after the replay's stopping point are speculative and not counted)
+    w, ev = event(name)
+    ll, surv, u0, l0, lnl_star = walk_inputs(w, ev, 60, 10, 8)
+    outs = []
+    for spec in (1, 2, 5, 16):
+        h = gwns.ns_init([gwns.make_config(w, priors(w, ev), precision=synth.PREC_MIXED_FF, spec_depth=spec)], [ev])
+        try:
+            outs.append(gwns.ns_hrss_batch(h, 0, surv, u0, l0, lnl_star, 3, 6, 2))
+        finally:
+            gwns.ns_free(h)
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+    gu, gl, gm, gn = outs[0]
+    assert np.all(gl > lnl_star) and np.all(gm > 0) and np.all(gn >= gm)
+
+
 def tiny_hrss():
     """The 4-parameter zero-noise event at 20-64 Hz (177 bins), 30 live points, k = 15."""
     from dataclasses import replace
