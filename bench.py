@@ -815,6 +815,9 @@ def run_profile_case(args):
             for w, e in zip(ws, evs)]
     h = gwns.ns_init(cfgs, evs)
     try:
+        if args.relbin > 0.0:
+            for e, ev in enumerate(evs):
+                gwns.ns_relbin_set(h, e, gwns.ns_relbin_edges(ev.f_min, ev.df, ev.n_bins, args.relbin), ev.theta_inj)
         for _ in range(args.profile_batches):
             _, p = gwns.ns_step(h, 1, len(evs))
         print(json.dumps(p[0]))
