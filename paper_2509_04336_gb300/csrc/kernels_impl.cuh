@@ -1449,8 +1449,9 @@ __global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restri
 //     takes the first inside the slice.
 // The chain, the moves and the likelihood-call counts are those of the one-candidate kernel (calls
 // of candidates after the replay's stopping point are counted in n_spec only); per round at most
-// task.spec candidates (1 .. kHrssQ).  Directions: warp 0's lanes draw the normals (Box-Muller on
-// the Philox blocks of hrss_kernel) and form d = C z / |z| row by row in the same order.
+// task.spec candidates (1 .. kHrssQ).  Directions do not depend on the walker's position: the
+// whole CTA forms those of 32 moves at a time (Box-Muller on the Philox blocks of hrss_kernel,
+// d = C z / |z| row by row in the same order).
 constexpr int kHrssQ = 16;
 
 template <int NDET, int WF>
@@ -1465,13 +1466,19 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
   __shared__ float wsums[WF == 1 ? kHrssQ : 1][kWarps][2 * kMaxVals];
   __shared__ double s_rbl[kHrssQ];
   __shared__ int s_rbk[kHrssQ];
-  __shared__ double x[kMaxDim], dvec[kMaxDim], zn[kMaxDim + 1];
+  __shared__ double x[kMaxDim];
+  __shared__ double zn_all[32][kMaxDim + 1];     // normals of the next 32 moves
+  __shared__ double dir_all[32][kMaxDim];        // their directions d = C z / |z|
   __shared__ double ct[kHrssQ];              // t of each candidate of the round, in evaluation order
   __shared__ double cpt[kHrssQ][kMaxDim];    // its point
+  __shared__ ff cf[kHrssQ][kMaxDim];         // the point as float pairs
+  __shared__ double s_u[kHrssQ];             // the round's shrinkage draws
+  __shared__ int s_oob[kHrssQ];              // the point lies outside the cube
+  __shared__ int ins_c[kHrssQ];              // each slot's ln L exceeds ln L*
   __shared__ int cslot[kHrssQ];              // its likelihood slot, -1 for a point outside the cube
   __shared__ double lnl_c[kHrssQ];           // ln L of each slot
   __shared__ int kend_c[kHrssQ];             // grid bins each slot's evaluation touched
-  __shared__ int s_nc, s_nin, s_newmove, s_exit, s_t;
+  __shared__ int s_nc, s_nin, s_newmove, s_exit, s_t, s_mode, s_nsh;
   const WalkTask& T = tasks[blk_task[blockIdx.x]];
   const int j = blk_local[blockIdx.x];
   const EventDev& ev = evs[T.event];
@@ -1504,32 +1511,39 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
   }
   __syncthreads();
   while (!s_exit) {
-    // A. warp 0: a new move's direction and bracket when the last move ended; the round's
-    //    candidates and their points
-    if (warp == 0) {
-      if (s_newmove) {
-        if (lane < (D + 3) / 4) {
-          const Philox4 b = philox4x64((uint64_t)s_t, wid, it, 32ull + (uint64_t)lane, T.key0, T.key1);
-          for (int q = 0; q < 2; ++q) {
-            const double r = sqrt(-2.0 * log(rand_open_unit(b.v[2 * q])));
-            double sn, cs;
-            sincospi(2.0 * rand_open_unit(b.v[2 * q + 1]), &sn, &cs);
-            const int i0 = 4 * lane + 2 * q;
-            if (i0 < D) zn[i0] = r * cs;
-            if (i0 + 1 < D) zn[i0 + 1] = r * sn;
-          }
+    // A1. the directions of the next 32 moves, on the whole CTA, when a block of moves begins:
+    //     a direction depends on its move's Philox counter only, not on the walker's position
+    if (s_newmove && (s_t & 31) == 0) {
+      const int base = s_t, nm = min(32, n_steps - base), nb = (D + 3) / 4;
+      for (int q = threadIdx.x; q < nm * nb; q += kThreads) {
+        const int mv = q / nb, c = q - mv * nb;
+        const Philox4 b = philox4x64((uint64_t)(base + mv), wid, it, 32ull + (uint64_t)c, T.key0, T.key1);
+        for (int h = 0; h < 2; ++h) {
+          const double r = sqrt(-2.0 * log(rand_open_unit(b.v[2 * h])));
+          double sn, cs;
+          sincospi(2.0 * rand_open_unit(b.v[2 * h + 1]), &sn, &cs);
+          const int i0 = 4 * c + 2 * h;
+          if (i0 < D) zn_all[mv][i0] = r * cs;
+          if (i0 + 1 < D) zn_all[mv][i0 + 1] = r * sn;
         }
-        __syncwarp();
-        if (lane < D) {
-          double nz = 0.0;
-          for (int i = 0; i < D; ++i) nz += zn[i] * zn[i];
-          nz = sqrt(nz);
-          double acc = 0.0;
-          for (int k = 0; k <= lane; ++k) acc += chol[lane * D + k] * zn[k];
-          dvec[lane] = acc / nz;
-        }
-        __syncwarp();
       }
+      __syncthreads();
+      for (int q = threadIdx.x; q < nm * D; q += kThreads) {
+        const int mv = q / D, i = q - mv * D;
+        double nz = 0.0;
+        for (int k = 0; k < D; ++k) nz += zn_all[mv][k] * zn_all[mv][k];
+        nz = sqrt(nz);
+        double acc = 0.0;
+        for (int k = 0; k <= i; ++k) acc += chol[i * D + k] * zn_all[mv][k];
+        dir_all[mv][i] = acc / nz;
+      }
+      __syncthreads();
+    }
+    // A2. warp 0: a new move's bracket; the round's candidates (shrinkage draws on the lanes) and
+    //     their points ((candidate, coordinate) pairs over the lanes)
+    if (warp == 0) {
+      const int tm = s_t;
+      const double* dv = dir_all[tm & 31];
       if (lane == 0) {
         if (s_newmove) {
           const Philox4 b = philox4x64((uint64_t)t, wid, it, 40ull, T.key0, T.key1);
@@ -1541,8 +1555,20 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
           left_on = jl > 0;
           right_on = kr > 0;
         }
+        s_mode = (left_on || right_on) ? 0 : min(Q, kHrssMaxShrink - nsh);
+        s_nsh = nsh;
+      }
+      __syncwarp();
+      const int S = s_mode;
+      if (lane < S) {
+        const int jj = s_nsh + lane;
+        const Philox4 b = philox4x64((uint64_t)tm, wid, it, 48ull + (uint64_t)(jj >> 2), T.key0, T.key1);
+        s_u[lane] = rand_open_unit(b.v[jj & 3]);
+      }
+      __syncwarp();
+      if (lane == 0) {
         int nc = 0;
-        if (left_on || right_on) {
+        if (S == 0) {
           // the next ends of both sides, as if every one were inside the slice
           int ql = left_on ? min(jl, Q) : 0;
           int qr = right_on ? min(kr, Q) : 0;
@@ -1555,12 +1581,9 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
           s_nc = nc | (ql << 8);
         } else {
           // the next shrinkage candidates, as if every one were rejected
-          const int S = min(Q, kHrssMaxShrink - nsh);
           double l2 = lo, h2 = hi;
           for (int q = 0; q < S; ++q) {
-            const int jj = nsh + q;
-            const Philox4 b = philox4x64((uint64_t)t, wid, it, 48ull + (uint64_t)(jj >> 2), T.key0, T.key1);
-            const double tc = l2 + (h2 - l2) * rand_open_unit(b.v[jj & 3]);
+            const double tc = l2 + (h2 - l2) * s_u[q];
             ct[nc++] = tc;
             if (tc < 0.0) l2 = tc;
             else h2 = tc;
@@ -1570,27 +1593,28 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
       }
       __syncwarp();
       const int nc = s_nc & 255;
-      int inb = 0;
-      if (lane < nc) {
-        const double tc = ct[lane];
-        inb = 1;
-        for (int i = 0; i < D; ++i) {
-          double v = x[i] + tc * dvec[i];
-          if (ev.prior[ev.dim_param[i]].periodic) v -= floor(v);
-          cpt[lane][i] = v;
-          if (!(v >= 0.0 && v <= 1.0)) inb = 0;
-        }
+      if (lane < nc) s_oob[lane] = 0;
+      __syncwarp();
+      for (int q = lane; q < nc * D; q += 32) {
+        const int c = q / D, i = q - c * D;
+        double v = x[i] + ct[c] * dv[i];
+        if (ev.prior[ev.dim_param[i]].periodic) v -= floor(v);
+        cpt[c][i] = v;
+        cf[c][i] = ff_from_double(v);
+        if (!(v >= 0.0 && v <= 1.0)) atomicOr(&s_oob[c], 1);
       }
+      __syncwarp();
+      const int inb = (lane < nc && s_oob[lane] == 0) ? 1 : 0;
       const unsigned im = __ballot_sync(0xffffffffu, inb);
-      const int slot = __popc(im & ((1u << lane) - 1u));
-      if (lane < nc) {
-        cslot[lane] = inb ? slot : -1;
-        if (inb) {
-#pragma unroll
-          for (int d = 0; d < kMaxDim; ++d) propf[slot][d] = d < D ? ff_from_double(cpt[lane][d]) : ff_make(0.0f);
-        }
-      }
+      if (lane < nc) cslot[lane] = inb ? __popc(im & ((1u << lane) - 1u)) : -1;
       if (lane == 0) s_nin = __popc(im);
+      __syncwarp();
+      // the in-cube candidates' coordinates in slot order
+      for (int q = lane; q < nc * kMaxDim; q += 32) {
+        const int c = q / kMaxDim, d = q - c * kMaxDim;
+        const int sl = cslot[c];
+        if (sl >= 0) propf[sl][d] = d < D ? cf[c][d] : ff_make(0.0f);
+      }
     }
     __syncthreads();
     const int nin = s_nin;
@@ -1677,6 +1701,7 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
         }
         lnl_c[lane] = l;
         kend_c[lane] = kb;
+        ins_c[lane] = l > lnl_star ? 1 : 0;
       }
       __syncwarp();
       if (lane == 0) {
@@ -1691,7 +1716,7 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
             if (sl >= 0) {
               ++calls;
               n_bins += kend_c[sl];
-              ins = lnl_c[sl] > lnl_star;
+              ins = ins_c[sl] != 0;
             }
             if (ins) {
               lo -= 1.0;
@@ -1706,7 +1731,7 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
             if (sl >= 0) {
               ++calls;
               n_bins += kend_c[sl];
-              ins = lnl_c[sl] > lnl_star;
+              ins = ins_c[sl] != 0;
             }
             if (ins) {
               hi += 1.0;
@@ -1721,7 +1746,7 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
             if (sl >= 0) {
               ++calls;
               n_bins += kend_c[sl];
-              if (lnl_c[sl] > lnl_star) {
+              if (ins_c[sl]) {
                 for (int d = 0; d < D; ++d) x[d] = cpt[i][d];
                 lnl = lnl_c[sl];
                 ++moves;
