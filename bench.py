@@ -773,12 +773,18 @@ def run_logz_convergence(args):
             ("de_240_50000", {"naccept": 240, "maxmcmc": 50000}, {}),
             ("hrss_22", {}, {"hrss_moves": 22}), ("hrss_66", {}, {"hrss_moves": 66}),
             ("hrss_198", {}, {"hrss_moves": 198})]
+    if args.workload.endswith("_flow"):
+        # the learned proposal at the default walk settings against longer DE walks and HRSS
+        arms = [("de_60_5000", {}, {}), ("de_240_50000", {"naccept": 240, "maxmcmc": 50000}, {}),
+                ("flow_0.5", {}, {"p_flow": 0.5, "flow_layers": 8}),
+                ("flow_0.9", {}, {"p_flow": 0.9, "flow_layers": 8}), ("hrss_198", {}, {"hrss_moves": 198})]
     out = {a[0]: [] for a in arms}
     for sd in range(args.logz_seeds):
         w0, ev = library_event(base, sd, local)
         w0 = replace(w0, seed=base.seed + sd)
+        edges = gwns.ns_relbin_edges(ev.f_min, ev.df, ev.n_bins, args.relbin) if args.relbin > 0.0 else None
         for tag, wk, ck in arms:
-            r = run_to_logz(gwns, replace(w0, **wk), ev, synth.PREC_MIXED_FF, local, **ck)
+            r = run_to_logz(gwns, replace(w0, **wk), ev, synth.PREC_MIXED_FF, local, relbin_edges=edges, **ck)
             out[tag].append(r)
             print(json.dumps({"seed": sd, "arm": tag, "log_z": r["log_z"], "log_z_err": r["log_z_err"],
                               "seconds": r["seconds"], "n_like": r["n_like"], "iterations": r["iterations"]}),
@@ -796,7 +802,8 @@ def run_logz_convergence(args):
                         "mean_n_like": float(np.mean([r["n_like"] for r in out[tag]])),
                         "mean_lnl_evals_per_ess": float(np.mean([r["lnl_evals_per_ess"] for r in out[tag]]))}
     print(json.dumps({"metric": "ln Z against the inner kernel's decorrelation (float-float mode)",
-                      "workload": WORKLOAD_DESCRIPTIONS[args.workload], "seeds": args.logz_seeds, "arms": summary}))
+                      "workload": WORKLOAD_DESCRIPTIONS[args.workload], "seeds": args.logz_seeds,
+                      "relbin_eps_rad": args.relbin or None, "arms": summary}))
     return 0
 
 

@@ -72,8 +72,6 @@ __device__ inline void partials(const EventDev& ev, const WalkerParams& P, int s
       if (PREC == 1) {
         for (int k = start; k < P.k_end; k += stride) bin_accumulate_mixed<NDET>(ev, P, k, acc);
       } else {
-        // two bins a pass: their independent phase chains interleave
-#pragma unroll 2
         for (int k = start; k < P.k_end; k += stride) bin_accumulate_ff<NDET>(ev, P, k, acc);
       }
 #pragma unroll
