@@ -338,28 +338,43 @@ __device__ inline void tf2_split_second(int part, const EventDev& ev, const TF2P
 // above, then the quantities of phenomd_extra<true> -- the ringdown fit, the pseudo-PN and
 // continuity constants and the region coefficients in float-float, the bin boundaries by
 // float-float comparisons, the ringdown frequency, damping and amplitude shape in FP32 (the
-// FP64 path's FAST variant rounds the same quantities to FP32).
-__device__ inline void phenomd_setup_ff(const EventDev& ev, const ff* x, WalkerParams& p) {
-  FFCore c;
-  ff_core(ev, x, c);
-  ff_tf2_coeffs(c, p);
+// FP64 path's FAST variant rounds the same quantities to FP32).  Two halves that depend on the
+// TaylorF2 core only: pd_chain (continuity constants, region coefficients, phase constants) and
+// pd_bins_amp (region boundaries, amplitude shape); the one-lane setup runs both, the split setup
+// runs them on different warps.
+// Quantities both halves need: mass scales of the ringdown model and the ringdown frequency and
+// damping (units of 1/M, FP32).
+struct PDPro {
+  ff eta, inv2pe, piM, M, M13, lnM;
+  float qf32, etaf, at, af, mfin, om, qfac, frd, fd;
+};
+__device__ inline PDPro pd_prologue(const FFCore& c) {
+  PDPro r;
+  r.eta = c.eta;
+  r.inv2pe = ff_div(ff_make(1.0f), ff_mul(GWNS_FF(2.0 * kPi), r.eta));
+  r.piM = ff_mul(ff_mul(c.c1, c.c1), c.c1);
+  r.M = ff_mul(r.piM, GWNS_FF(1.0 / kPi));
+  r.M13 = ff_mul(c.c1, GWNS_FF(1.0 / 1.4645918875615231));   // M^(1/3)
+  r.lnM = ff_sub(c.lpm, GWNS_FF(kLnPi));
+  r.qf32 = c.q.h;
+  r.etaf = r.eta.h;
+  const float qf32 = r.qf32, etaf = r.etaf;
+  r.at = (c.chi1.h + c.chi2.h * qf32 * qf32) / (1.0f + qf32 * qf32);
+  const float at = r.at;
+  r.af = at + at * etaf * (-0.1229f * at + 0.4537f * etaf - 2.8904f) +
+         etaf * (2.0f * 1.7320508075688772f + -3.5171f * etaf + 2.5763f * etaf * etaf);
+  r.mfin = 1.0f - ((float)kPdE1 * etaf + (float)kPdE2 * etaf * etaf);
+  r.om = 1.5251f - 1.1568f * powf(1.0f - r.af, 0.1292f);
+  r.qfac = 0.7000f + 1.4187f * powf(1.0f - r.af, -0.4990f);
+  r.frd = r.om / (2.0f * (float)kPi * r.mfin);
+  r.fd = r.frd / (2.0f * r.qfac);
+  return r;
+}
+__device__ inline void pd_chain(const FFCore& c, WalkerParams& p) {
   PhenomExtra& e = p.pd;
-  const ff eta = c.eta;
-  const ff inv2pe = ff_div(ff_make(1.0f), ff_mul(GWNS_FF(2.0 * kPi), eta));
-  const ff piM = ff_mul(ff_mul(c.c1, c.c1), c.c1);
-  const ff M = ff_mul(piM, GWNS_FF(1.0 / kPi));
-  const ff M13 = ff_mul(c.c1, GWNS_FF(1.0 / 1.4645918875615231));   // M^(1/3)
-  const ff lnM = ff_sub(c.lpm, GWNS_FF(kLnPi));
-  // ringdown frequency and damping (units of 1/M), FP32
-  const float qf32 = c.q.h, etaf = eta.h;
-  const float at = (c.chi1.h + c.chi2.h * qf32 * qf32) / (1.0f + qf32 * qf32);
-  const float af = at + at * etaf * (-0.1229f * at + 0.4537f * etaf - 2.8904f) +
-                   etaf * (2.0f * 1.7320508075688772f + -3.5171f * etaf + 2.5763f * etaf * etaf);
-  const float mfin = 1.0f - ((float)kPdE1 * etaf + (float)kPdE2 * etaf * etaf);
-  const float om = 1.5251f - 1.1568f * powf(1.0f - af, 0.1292f);
-  const float qfac = 0.7000f + 1.4187f * powf(1.0f - af, -0.4990f);
-  const float frd = om / (2.0f * (float)kPi * mfin);
-  const float fd = frd / (2.0f * qfac);
+  const PDPro pro = pd_prologue(c);
+  const ff eta = pro.eta, inv2pe = pro.inv2pe, M = pro.M, M13 = pro.M13, lnM = pro.lnM;
+  const float frd = pro.frd, fd = pro.fd;
   // inspiral at x1: value and slope of the TaylorF2 part from constant powers of v1
   ff s = ff_make(0.0f), ds = ff_make(0.0f);
   // v1^(k - 5), k = 0..7
@@ -422,6 +437,15 @@ __device__ inline void phenomd_setup_ff(const EventDev& ev, const ff* x, WalkerP
   const ff ph0_mr = ff_add(ff_mul(a0, inv2pe), tail);
   e.ph0_int_h = ph0_int.h; e.ph0_int_l = ph0_int.l;
   e.ph0_mr_h = ph0_mr.h; e.ph0_mr_l = ph0_mr.l;
+}
+
+__device__ inline void pd_bins_amp(const EventDev& ev, const FFCore& c, WalkerParams& p) {
+  PhenomExtra& e = p.pd;
+  const PDPro pro = pd_prologue(c);
+  const ff inv2pe = pro.inv2pe, M = pro.M;
+  const float etaf = pro.etaf, frd = pro.frd, fd = pro.fd;
+  const double x1 = kPdXIns;
+  const float x2 = 0.5f * frd;
   // region boundaries as bin indices
   const ff iM = ff_div(ff_make(1.0f), M);
   e.k1 = ff_bins_below(ev, ff_mul(GWNS_FF(x1), iM), true);
@@ -451,8 +475,62 @@ __device__ inline void phenomd_setup_ff(const EventDev& ev, const ff* x, WalkerP
   e.hc3f = 2.0f * (y0 - y1) + span * d0 + span * d1;
   e.frdf = frd; e.gdf = gd; e.g1gdf = (float)kPdG1 * gd; e.g2_gdf = (float)kPdG2 / gd;
   e.at_scalef = (float)kPdA4 * (inv2pe.h + inv2pe.l); e.at_cf = (float)kPdA5 * frd; e.at_invf = 1.0f / fd;
-  ff_projection(ev, c, p);
   p.hh_f = 0.0f;   // the IMRPhenomD form sums its template power per bin
+}
+
+__device__ inline void phenomd_setup_ff(const EventDev& ev, const ff* x, WalkerParams& p) {
+  FFCore c;
+  ff_core(ev, x, c);
+  ff_tf2_coeffs(c, p);
+  pd_chain(c, p);
+  pd_bins_amp(ev, c, p);
+  ff_projection(ev, c, p);
+}
+
+// The IMRPhenomD-form constants formed by the warps of a CTA at once, as tf2_split_first /
+// tf2_split_second: first pass (0) mass scales, ln(pi M), prefactor, mass ratio; (1) PN
+// coefficients and spin combinations; (2) sky, antenna patterns, delays; second pass (0, 1) the
+// TaylorF2 basis coefficients, (2) the phase constant and pd_chain, (3) pd_bins_amp.  The
+// arithmetic of every quantity is the one-lane setup's.
+struct PDPart {
+  TF2Part t;
+  ff q, eta, delta, chis, chia, chi1, chi2;
+};
+
+__device__ inline void pd_split_first(int part, const EventDev& ev, const ff* x, PDPart& s, WalkerParams& p) {
+  tf2_split_first(part, ev, x, s.t, p);
+  if (part == 0) {
+    FFCore c;
+    c.q = ff_prior_lin(ev, 1, x);
+    ff_mass_ratio(c);
+    s.q = c.q;
+    s.eta = c.eta;
+    s.delta = c.delta;
+  } else if (part == 1) {
+    s.chi1 = ff_prior_lin(ev, 2, x);
+    s.chi2 = ff_prior_lin(ev, 3, x);
+    s.chis = ff_ldexp(ff_add(s.chi1, s.chi2), -1);
+    s.chia = ff_ldexp(ff_sub(s.chi1, s.chi2), -1);
+  }
+}
+
+__device__ inline void pd_split_second(int part, const EventDev& ev, const PDPart& s, WalkerParams& p) {
+  FFCore c;
+  const TF2Part& t = s.t;
+  c.pre = t.pre; c.c1 = t.c1; c.ci1 = t.ci1; c.ci2 = t.ci2; c.ci3 = t.ci3; c.ci5 = t.ci5; c.lpm = t.lpm;
+  c.phic = t.phic;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) c.a[j] = t.a[j];
+  c.al5 = t.al5;
+  c.q = s.q; c.eta = s.eta; c.delta = s.delta; c.chis = s.chis; c.chia = s.chia; c.chi1 = s.chi1; c.chi2 = s.chi2;
+  if (part == 0) ff_tf2_coeff_range(c, 0, 4, p);
+  else if (part == 1) ff_tf2_coeff_range(c, 4, 8, p);
+  else if (part == 2) {
+    ff_tf2_phase0(c, p);
+    pd_chain(c, p);
+  } else {
+    pd_bins_amp(ev, c, p);
+  }
 }
 
 }  // namespace gwns

@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cstdio>
+#include <type_traits>
 
 #include "flow.cuh"
 #include "gwns_internal.h"
@@ -39,11 +40,14 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// The watchdog test of a walk's thread 0: a host-set abort flag, or the task's time budget
-// (nanoseconds since the CTA started) spent.
-__device__ __forceinline__ bool walk_should_stop(const WalkTask& T, uint64_t t0) {
-  if (T.abort && *(volatile const int32_t*)T.abort != 0) return true;
-  return T.budget_ns != 0ull && global_ns() - t0 > T.budget_ns;
+// The watchdog of a walk's thread 0: a host-set abort flag (read at the start of a round, so that
+// the load's latency overlaps the round) and the task's time budget (nanoseconds since the CTA
+// started).
+__device__ __forceinline__ int walk_abort_flag(const WalkTask& T) {
+  return T.abort ? *(volatile const int32_t*)T.abort : 0;
+}
+__device__ __forceinline__ bool walk_should_stop(const WalkTask& T, uint64_t t0, int abort_flag) {
+  return abort_flag != 0 || (T.budget_ns != 0ull && global_ns() - t0 > T.budget_ns);
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -717,6 +721,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
   }
   int t = 0;
   while (t < n_steps) {
+    const int abort_flag = threadIdx.x == 0 ? walk_abort_flag(T) : 0;
     const int W = min(window, n_steps - t);
     // 1a. every thread screens one candidate step in FP32
     int maybe = 0;
@@ -914,7 +919,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
         }
       }
       n_spec += nin;
-      if (walk_should_stop(T, t0)) {   // watchdog: end the walk after this round
+      if (walk_should_stop(T, t0, abort_flag)) {   // watchdog: end the walk after this round
         nxt = n_steps;
         if (T.status) atomicOr(T.status, 1);
       }
@@ -956,9 +961,10 @@ __device__ __forceinline__ ff ff_wrap_unit(ff x) {
 //     arithmetic (the DE scale's logarithm, the survivors' float-float difference, the periodic
 //     wrap, the bounds test) -- there is no FP32 screen and no one-warp recheck -- and a ballot
 //     compacts the first m in-bounds moves;
-//  2. the TaylorF2 setup of the round runs on all four warps at once (tf2_split_first /
-//     tf2_split_second: four independent chains, then the products); the IMRPhenomD-form
-//     setup, a small part of its round, stays on one rotating warp;
+//  2. the proposal constants of the round run on all four warps at once (tf2_split_first /
+//     tf2_split_second, pd_split_first / pd_split_second: independent chains, then the
+//     products; the IMRPhenomD form's continuity constants and its region boundaries and
+//     amplitude shape on different warps);
 //  3. the likelihoods: TaylorF2 one warp per proposal, the IMRPhenomD form the whole CTA per
 //     proposal;
 //  4. warp 0 assembles ln L of every proposal in float-float and finds the first acceptance
@@ -976,7 +982,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   constexpr int NV = NVals<NDET, WF>::value;
   __shared__ WalkerParams P[kSpecMax];
   __shared__ ff propf[kSpecMax][kMaxDim];
-  __shared__ TF2Part parts[WF == 0 ? kSpecMax : 1];
+  __shared__ std::conditional_t<WF == 0, TF2Part, PDPart> parts[kSpecMax];
   __shared__ int cstep[kSpecMax];
   __shared__ float part_sums[kSpecMax][2 * kMaxVals];
   __shared__ double s_rbl[kSpecMax];   // relative binning: ln L of each proposal
@@ -1005,7 +1011,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   if (WF == 0) m = min((m + 3) & ~3, kSpecMax);
   const int window = min(kThreads, max(32, 4 * m));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool split = WF == 0 && ev.ff_setup;
+  const bool split = ev.ff_setup;
   if (threadIdx.x < D) {
     const double v = T.u0[(size_t)j * D + threadIdx.x];
     u[threadIdx.x] = v;
@@ -1036,6 +1042,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   }
   int t = 0;
   while (t < n_steps) {
+    const int abort_flag = threadIdx.x == 0 ? walk_abort_flag(T) : 0;
     const int W = min(window, n_steps - t);
     // 1. the exact move of one candidate step per thread
     const int step = t + (int)threadIdx.x;
@@ -1136,9 +1143,15 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
     // 2. proposal constants
     if (nin > 0) {
       if (split) {
-        if (lane < nin) tf2_split_first(warp, ev, propf[lane], parts[lane], P[lane]);
+        if (lane < nin) {
+          if constexpr (WF == 0) tf2_split_first(warp, ev, propf[lane], parts[lane], P[lane]);
+          else pd_split_first(warp, ev, propf[lane], parts[lane], P[lane]);
+        }
         __syncthreads();
-        if (lane < nin) tf2_split_second(warp, ev, parts[lane], P[lane]);
+        if (lane < nin) {
+          if constexpr (WF == 0) tf2_split_second(warp, ev, parts[lane], P[lane]);
+          else pd_split_second(warp, ev, parts[lane], P[lane]);
+        }
       } else if (warp == sw && lane < nin) {
         if (ev.ff_setup) {
           if (WF == 0) taylorf2_setup_ff(ev, propf[lane], P[lane]);
@@ -1245,7 +1258,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
             else s_needq = 1;
           }
         }
-        if (walk_should_stop(T, t0)) {   // watchdog: end the walk after this round
+        if (walk_should_stop(T, t0, abort_flag)) {   // watchdog: end the walk after this round
           nxt = n_steps;
           if (T.status) atomicOr(T.status, 1);
         }
@@ -1321,7 +1334,7 @@ __global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restri
   __syncthreads();
   for (int t = 0; t < n_steps; ++t) {
     if (threadIdx.x == 0) {
-      s_stop = walk_should_stop(T, t0) ? 1 : 0;
+      s_stop = walk_should_stop(T, t0, walk_abort_flag(T)) ? 1 : 0;
       if (s_stop && T.status) atomicOr(T.status, 1);
       double z[kMaxDim];
       for (int c = 0; 4 * c < D; ++c) {
@@ -1461,7 +1474,7 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
   constexpr int NV = NVals<NDET, WF>::value;
   __shared__ WalkerParams P[kHrssQ];
   __shared__ ff propf[kHrssQ][kMaxDim];
-  __shared__ TF2Part parts[WF == 0 ? kHrssQ : 1];
+  __shared__ std::conditional_t<WF == 0, TF2Part, PDPart> parts[kHrssQ];
   __shared__ float part_sums[kHrssQ][2 * kMaxVals];
   __shared__ float wsums[WF == 1 ? kHrssQ : 1][kWarps][2 * kMaxVals];
   __shared__ double s_rbl[kHrssQ];
@@ -1491,7 +1504,7 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
   const double* chol = T.chol;
   const int Q = T.spec < 1 ? 1 : (T.spec > kHrssQ ? kHrssQ : T.spec);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool split = WF == 0 && ev.ff_setup;
+  const bool split = ev.ff_setup;
   const bool rb = ev.rb_nb > 0;
   const int sw = (int)(blockIdx.x % (unsigned)kWarps);   // the setup warp of the non-split setups
   if ((int)threadIdx.x < D) x[threadIdx.x] = T.u0[(size_t)j * D + threadIdx.x];
@@ -1621,9 +1634,15 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
     // B. the candidates' constants
     if (nin > 0) {
       if (split) {
-        if (lane < nin) tf2_split_first(warp, ev, propf[lane], parts[lane], P[lane]);
+        if (lane < nin) {
+          if constexpr (WF == 0) tf2_split_first(warp, ev, propf[lane], parts[lane], P[lane]);
+          else pd_split_first(warp, ev, propf[lane], parts[lane], P[lane]);
+        }
         __syncthreads();
-        if (lane < nin) tf2_split_second(warp, ev, parts[lane], P[lane]);
+        if (lane < nin) {
+          if constexpr (WF == 0) tf2_split_second(warp, ev, parts[lane], P[lane]);
+          else pd_split_second(warp, ev, parts[lane], P[lane]);
+        }
       } else if (warp == sw && lane < nin) {
         if (ev.ff_setup) {
           if (WF == 0) taylorf2_setup_ff(ev, propf[lane], P[lane]);
@@ -1766,7 +1785,7 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
         s_newmove = move_end ? 1 : 0;
         s_t = t;
         if (t >= n_steps) s_exit = 1;
-        if (!s_exit && walk_should_stop(T, t0)) {   // watchdog: the walker stays where it is
+        if (!s_exit && walk_should_stop(T, t0, walk_abort_flag(T))) {   // watchdog: the walker stays where it is
           s_exit = 1;
           if (T.status) atomicOr(T.status, 1);
         }
