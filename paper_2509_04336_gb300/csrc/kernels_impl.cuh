@@ -1460,6 +1460,10 @@ __global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restri
 //     t_j = lo_j + (hi_j - lo_j) U_j, where (lo_j, hi_j) is the bracket left by rejecting
 //     t_1 .. t_{j-1}; a round holds the next candidates as if all were rejected, and the replay
 //     takes the first inside the slice.
+// A stepping-out round holds up to max(1, spec/4) ends a side and fills the rest of the round
+// with the first shrinkage candidates of the bracket as it stands: they are the move's next
+// candidates exactly when every side still extending stops at its first end in the round, and
+// the replay uses them only then -- a move whose bracket does not grow ends in one round.
 // The chain, the moves and the likelihood-call counts are those of the one-candidate kernel (calls
 // of candidates after the replay's stopping point are counted in n_spec only); per round at most
 // task.spec candidates (1 .. kHrssQ).  Directions do not depend on the walker's position: the
@@ -1568,8 +1572,22 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
           left_on = jl > 0;
           right_on = kr > 0;
         }
-        s_mode = (left_on || right_on) ? 0 : min(Q, kHrssMaxShrink - nsh);
+        int ql = 0, qr = 0, S;
+        if (left_on || right_on) {
+          // stepping out: up to max(1, Q/4) next ends a side, the rest of the round's candidates
+          // the shrinkage draws from the current bracket, which hold if every side still extending
+          // stops at its first end in this round
+          const int qs = max(1, Q / 4);
+          ql = left_on ? min(jl, qs) : 0;
+          qr = right_on ? min(kr, qs) : 0;
+          if (ql + qr > Q) qr = Q - ql;
+          S = min(Q - ql - qr, kHrssMaxShrink - nsh);
+        } else {
+          S = min(Q, kHrssMaxShrink - nsh);
+        }
+        s_mode = S;
         s_nsh = nsh;
+        s_nc = (ql << 8) | (qr << 16);
       }
       __syncwarp();
       const int S = s_mode;
@@ -1581,17 +1599,20 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
       __syncwarp();
       if (lane == 0) {
         int nc = 0;
-        if (S == 0) {
-          // the next ends of both sides, as if every one were inside the slice
-          int ql = left_on ? min(jl, Q) : 0;
-          int qr = right_on ? min(kr, Q) : 0;
-          if (ql + qr > Q) {
-            ql = min(ql, max(Q / 2, Q - qr));
-            qr = min(qr, Q - ql);
-          }
+        if (left_on || right_on) {
+          // the next ends of both sides, as if every one were inside the slice, then the
+          // shrinkage candidates of the bracket as it stands, as if each were rejected
+          const int ql = (s_nc >> 8) & 255, qr = (s_nc >> 16) & 255;
           for (int i = 0; i < ql; ++i) ct[nc++] = lo - (double)i;
           for (int i = 0; i < qr; ++i) ct[nc++] = hi + (double)i;
-          s_nc = nc | (ql << 8);
+          double l2 = lo, h2 = hi;
+          for (int q = 0; q < S; ++q) {
+            const double tc = l2 + (h2 - l2) * s_u[q];
+            ct[nc++] = tc;
+            if (tc < 0.0) l2 = tc;
+            else h2 = tc;
+          }
+          s_nc = nc | (ql << 8) | (qr << 16);
         } else {
           // the next shrinkage candidates, as if every one were rejected
           double l2 = lo, h2 = hi;
@@ -1727,8 +1748,13 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
         const int nc = s_nc & 255;
         n_spec += nin;
         bool move_end = false;
+        int sh0 = 0;          // first shrinkage candidate of the round
+        bool shrink = true;   // the round's shrinkage candidates are the move's next ones
         if (left_on || right_on) {
-          const int ql = s_nc >> 8;
+          const int ql = (s_nc >> 8) & 255, qr = (s_nc >> 16) & 255;
+          // the speculative shrinkage holds iff every side extending at the round's start stops
+          // at its first end here (the bracket is then the one the candidates were drawn in)
+          if ((left_on && ql == 0) || (right_on && qr == 0)) shrink = false;
           for (int i = 0; i < ql && left_on; ++i) {
             const int sl = cslot[i];
             bool ins = false;
@@ -1738,13 +1764,14 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
               ins = ins_c[sl] != 0;
             }
             if (ins) {
+              shrink = false;
               lo -= 1.0;
               if (--jl == 0) left_on = false;
             } else {
               left_on = false;
             }
           }
-          for (int i = ql; i < nc && right_on; ++i) {
+          for (int i = ql; i < ql + qr && right_on; ++i) {
             const int sl = cslot[i];
             bool ins = false;
             if (sl >= 0) {
@@ -1753,14 +1780,18 @@ __global__ void __launch_bounds__(kThreads, 4) hrss_kernel_ff(const EventDev* __
               ins = ins_c[sl] != 0;
             }
             if (ins) {
+              shrink = false;
               hi += 1.0;
               if (--kr == 0) right_on = false;
             } else {
               right_on = false;
             }
           }
-        } else {
-          for (int i = 0; i < nc; ++i) {
+          sh0 = ql + qr;
+          if (left_on || right_on) shrink = false;
+        }
+        if (shrink) {
+          for (int i = sh0; i < nc; ++i) {
             const int sl = cslot[i];
             if (sl >= 0) {
               ++calls;
