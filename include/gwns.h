@@ -169,7 +169,8 @@ typedef struct ns_progress {
     int64_t n_spec;       /* likelihoods evaluated by walks so far, including those   */
                           /* evaluated ahead and dropped after an earlier acceptance  */
     int32_t spec_depth;   /* speculation depth of the next batch                    */
-    int32_t reserved;
+    int32_t spec_cap;     /* the cap on it in force (chosen by the autotuner when the
+                             configuration leaves the depth automatic)                */
 } ns_progress;
 
 typedef struct ns_handle ns_handle;

@@ -646,7 +646,7 @@ static void fill_progress(ns_handle* h, ns_progress* p) {
     p[e].kernel_launches = h->kernel_launches;
     p[e].n_spec = S.n_spec_eval;
     p[e].spec_depth = S.spec;
-    p[e].reserved = 0;
+    p[e].spec_cap = S.spec_cap;
   }
 }
 

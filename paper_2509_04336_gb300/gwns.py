@@ -60,7 +60,7 @@ class ns_progress(C.Structure):
                 ("log_x", C.c_double), ("lnl_star", C.c_double), ("mean_accept", C.c_double),
                 ("n_steps", C.c_int32), ("done", C.c_int32), ("n_bins", C.c_int64), ("walk_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("n_spec", C.c_int64), ("spec_depth", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("spec_cap", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

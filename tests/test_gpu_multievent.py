@@ -64,3 +64,48 @@ def test_mixed_precision_events_run_to_termination():
             assert np.isfinite(lz) and err > 0 and info > 0 and n_like == p["n_like"]
     finally:
         gwns.ns_free(h)
+
+
+def test_speculation_autotuner_choice_and_chain():
+    # The speculation-depth autotuner (automatic depth): after the first batch the cap follows
+    # the cost structure (FP64, short likelihoods of < 1k active bins: 8); from iteration 64 a
+    # tuning pass tries every FP64 candidate cap {1, 2, 4, 8} in mirrored order and keeps one of
+    # them; the depth in force never exceeds the cap.  Any depth gives the chain of the one-step
+    # walk, so the tuned run equals a run at a fixed depth bit for bit.
+    evs = small_events(synth.PREC_FP64)
+    iters = 80
+    def run(spec):
+        cfgs = [replace_cfg(gwns.make_config(w, synth.priors_with_injection(w, ev), max_iter=iters, spec_depth=spec))
+                for w, ev in evs]
+        h = gwns.ns_init(cfgs, [ev for _, ev in evs])
+        caps, depths = [], []
+        try:
+            for b in range(iters):
+                _, prog = gwns.ns_step(h, 1, n_events=len(evs))
+                caps.append(prog[0]["spec_cap"])
+                depths.append([p["spec_depth"] for p in prog])
+            post = [gwns.ns_posterior(h, e) for e in range(len(evs))]
+        finally:
+            gwns.ns_free(h)
+        return prog, caps, depths, post
+
+    prog_a, caps, depths, post_a = run(0)
+    prog_f, _, _, post_f = run(3)
+    assert caps[1] == 8                                   # the cost-structure guess after batch 1
+    assert all(c in (1, 2, 4, 8) for c in caps[1:])
+    assert caps[-1] in (1, 2, 4, 8)
+    assert caps[64:72] == [1, 2, 4, 8, 8, 4, 2, 1]       # the tuning pass, one batch a candidate
+    assert len(set(caps[72:])) == 1                       # then its choice, kept
+    for c, ds in zip(caps[1:], depths[1:]):
+        assert all(1 <= d <= c for d in ds)
+    for e in range(len(evs)):
+        assert prog_a[e]["iterations"] == prog_f[e]["iterations"] == iters
+        assert prog_a[e]["n_like"] == prog_f[e]["n_like"]
+        assert prog_a[e]["log_z"] == prog_f[e]["log_z"]
+        assert np.array_equal(post_a[e][0], post_f[e][0])
+
+
+def replace_cfg(c):
+    # run every event to the batch cap: a stopping threshold nothing reaches
+    c.term_value = 1e-12
+    return c
