@@ -238,6 +238,30 @@ int ns_walk_batch_noalloc(ns_handle* h, int event, const double* live_u, int n_l
  * positive definite. */
 int ns_step(ns_handle* h, int max_batches, ns_progress* progress);
 
+/* ---- a batch in phases: walker sharding of one event over processes (one GPU each) ----
+ * ns_step runs a batch (Sec. 2.2.3) as deletion, walk and insertion on the device.  These calls
+ * run the same kernels one phase at a time, so that R processes holding identical handles (same
+ * events, configurations and seeds) can split the k walkers of a batch -- the walks are
+ * independent and each walker's chain depends only on its index (its Philox counters) -- and
+ * exchange the k walk outputs, k x (D + 1) FP64 plus counters, before the insertion:
+ *   ns_batch_begin   deletion, evidence update, starts (and the flow training or the HRSS
+ *                    covariance of the batch); blocks until done
+ *   ns_batch_walk    the walks of walkers [walker_begin, walker_end) of every event (clipped
+ *                    to each event's num_delete)
+ *   ns_batch_walk_io copies the walk outputs of walkers [walker_begin, walker_end) of one event
+ *                    out of the handle (write = 0) or into it (write = 1): u [n][D], lnl [n],
+ *                    n_accept [n], n_like [n], n_bins [n], n_spec [n] (n = end - begin), host or
+ *                    device pointers per ptr_kind (on the handle's stream; returns when done)
+ *   ns_batch_end     insertion, walk-length retune, termination; progress as ns_step's
+ * Every walker's outputs must be in the handle (walked here or written in) before ns_batch_end;
+ * run on every process, the sequence leaves every handle in the state ns_step would, bit for bit.
+ * Between ns_batch_begin and ns_batch_end, ns_step and checkpoints are refused (NS_ESTATE). */
+int ns_batch_begin(ns_handle* h);
+int ns_batch_walk(ns_handle* h, int64_t walker_begin, int64_t walker_end);
+int ns_batch_walk_io(ns_handle* h, int event, int64_t walker_begin, int64_t walker_end, double* u, double* lnl,
+                     int32_t* n_accept, int32_t* n_like, int64_t* n_bins, int64_t* n_spec, int ptr_kind, int write);
+int ns_batch_end(ns_handle* h, ns_progress* progress);
+
 /* Watchdog of the walks (failure detection on the device).  Every walk -- ns_walk_batch,
  * ns_walk_batch_noalloc, ns_hrss_batch and the walks of ns_step -- checks between its rounds
  * (HRSS: between moves) a time budget and an abort flag, and when either has run out it stops

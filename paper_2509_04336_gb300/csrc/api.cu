@@ -604,6 +604,7 @@ extern "C" void ns_free(ns_handle* h) {
   cudaFree(h->scratch_out.ptr);
   cudaFree(h->scratch_map.ptr);
   cudaFree(h->scratch_flow.ptr);
+  cudaFree(h->scratch_shard.ptr);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
   delete h;

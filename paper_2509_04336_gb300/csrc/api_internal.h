@@ -85,7 +85,8 @@ struct ns_handle {
   std::vector<gwns::EventHost> events;
   gwns::EventDev* d_events = nullptr;
   int32_t* d_status = nullptr;
-  gwns::Scratch scratch_in, scratch_out, scratch_map, scratch_flow;
+  gwns::Scratch scratch_in, scratch_out, scratch_map, scratch_flow, scratch_shard;
+  bool batch_open = false;   // ns_batch_begin ran; ns_batch_end closes the batch
   // nested sampling
   gwns::NsState* d_ns = nullptr;
   gwns::WalkTask* d_tasks = nullptr;

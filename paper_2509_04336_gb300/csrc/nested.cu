@@ -678,6 +678,7 @@ int set_spec_cap(ns_handle* h, int cap) {
 extern "C" int ns_step(ns_handle* h, int max_batches, ns_progress* progress) {
   if (!h) return set_error(nullptr, NS_EINVAL, "handle is NULL");
   if (max_batches < 0) return set_error(h, NS_EINVAL, "max_batches < 0");
+  if (h->batch_open) return set_error(h, NS_ESTATE, "a batch is open (ns_batch_end)");
   cudaSetDevice(h->device);
   cudaGetLastError();   // a stale error of an earlier call must not be reported here
   int r;
@@ -887,6 +888,7 @@ bool dev_read(FILE* f, T* d, size_t n) {
 
 extern "C" int ns_state_save(ns_handle* h, const char* path) {
   if (!h || !path) return set_error(h, NS_EINVAL, "null argument");
+  if (h->batch_open) return set_error(h, NS_ESTATE, "a batch is open (ns_batch_end)");
   cudaSetDevice(h->device);
   int r = download_states(h);
   if (r) return r;
@@ -909,6 +911,7 @@ extern "C" int ns_state_save(ns_handle* h, const char* path) {
 
 extern "C" int ns_state_load(ns_handle* h, const char* path) {
   if (!h || !path) return set_error(h, NS_EINVAL, "null argument");
+  if (h->batch_open) return set_error(h, NS_ESTATE, "a batch is open (ns_batch_end)");
   cudaSetDevice(h->device);
   FILE* f = fopen(path, "rb");
   if (!f) return set_error(h, NS_EIO, "cannot open %s", path);
@@ -969,4 +972,146 @@ extern "C" int ns_state_load(ns_handle* h, const char* path) {
       return cuda_fail(h, err, "state upload");
   }
   return download_states(h);
+}
+
+// ---------------------------------------------------------------- the batch in phases
+// ns_step runs deletion, walk and insertion of a batch as one graph.  These calls run the same
+// kernels one phase at a time, so that the walkers of a batch can be spread over processes (one
+// GPU each) that exchange the walk outputs between the phases: every process holds the same
+// handle state, runs the deletion and the insertion itself (deterministic and identical) and
+// walks its own range of walkers.
+namespace {
+int batch_checks(ns_handle* h, bool want_open) {
+  if (!h) return set_error(nullptr, NS_EINVAL, "handle is NULL");
+  if (h->batch_open != want_open)
+    return set_error(h, NS_ESTATE, want_open ? "no batch is open (ns_batch_begin)" : "a batch is open (ns_batch_end)");
+  cudaSetDevice(h->device);
+  cudaGetLastError();
+  return NS_OK;
+}
+}  // namespace
+
+extern "C" int ns_batch_begin(ns_handle* h) {
+  int r = batch_checks(h, false);
+  if (r) return r;
+  bool all_done = true;
+  for (auto& S : h->host_ns) all_done = all_done && S.done;
+  if (all_done) return set_error(h, NS_ESTATE, "every event has finished");
+  if ((r = ensure_dead_capacity(h, 1))) return r;
+  const int ne = (int)h->events.size();
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(h->d_status + 2, 0, sizeof(int32_t), h->stream)) != cudaSuccess)
+    return cuda_fail(h, e, "watchdog reset");
+  int64_t launches = 0;
+  select_kernel<<<ne, kSelThreads, 0, h->stream>>>(h->d_ns, h->d_tasks);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "select launch");
+  for (int ev = 0; ev < ne; ++ev)
+    if ((r = flow_enqueue_train(h, ev, h->stream, &launches)) || (r = flow_enqueue_table(h, ev, h->stream, &launches)))
+      return r;
+  launches += 1;
+  if (h->hrss) {
+    chol_kernel<<<ne, kSelThreads, 0, h->stream>>>(h->d_ns, h->d_tasks);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "covariance launch");
+    launches += 1;
+  }
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "batch begin");
+  h->kernel_launches += launches;
+  h->batch_open = true;
+  return NS_OK;
+}
+
+extern "C" int ns_batch_walk(ns_handle* h, int64_t walker_begin, int64_t walker_end) {
+  int r = batch_checks(h, true);
+  if (r) return r;
+  if (walker_begin < 0 || walker_end < walker_begin) return set_error(h, NS_EINVAL, "bad walker range");
+  std::vector<int32_t> bt, bl;
+  for (size_t ev = 0; ev < h->events.size(); ++ev) {
+    const int64_t k = h->events[ev].ns.k;
+    for (int64_t j = walker_begin; j < walker_end && j < k; ++j) {
+      bt.push_back((int32_t)ev);
+      bl.push_back((int32_t)j);
+    }
+  }
+  const int nb = (int)bt.size();
+  if (nb == 0) return NS_OK;
+  if ((r = ensure_scratch(h, h->scratch_shard, sizeof(int32_t) * 2 * (size_t)nb))) return r;
+  int32_t* d_bt = (int32_t*)h->scratch_shard.ptr;
+  int32_t* d_bl = d_bt + nb;
+  bt.insert(bt.end(), bl.begin(), bl.end());
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d_bt, bt.data(), sizeof(int32_t) * bt.size(), cudaMemcpyHostToDevice, h->stream)))
+    return cuda_fail(h, e, "walker map upload");
+  if (h->walk_events.size() < 2) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t ev;
+      if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(h, e, "event create");
+      h->walk_events.push_back(ev);
+    }
+  }
+  if ((e = cudaEventRecord(h->walk_events[0], h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+  e = h->hrss ? launch_hrss(h->precision, h->waveform, h->max_det, h->d_events, h->d_tasks, d_bt, d_bl, nb, h->stream)
+              : launch_walk(h->precision, h->waveform, h->max_det, h->d_events, h->d_tasks, d_bt, d_bl, nb, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "walk launch");
+  if ((e = cudaEventRecord(h->walk_events[1], h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "walk");
+  float ms = 0.f;
+  if ((e = cudaEventElapsedTime(&ms, h->walk_events[0], h->walk_events[1])) != cudaSuccess)
+    return cuda_fail(h, e, "walk timing");
+  h->walk_ms += ms;
+  h->kernel_launches += 1;
+  return NS_OK;
+}
+
+extern "C" int ns_batch_walk_io(ns_handle* h, int event, int64_t walker_begin, int64_t walker_end, double* u,
+                                double* lnl, int32_t* n_accept, int32_t* n_like, int64_t* n_bins, int64_t* n_spec,
+                                int ptr_kind, int write) {
+  int r = batch_checks(h, true);
+  if (r) return r;
+  if (event < 0 || event >= (int)h->events.size()) return set_error(h, NS_EINVAL, "event out of range");
+  const NsState& S = h->events[event].ns;
+  if (walker_begin < 0 || walker_end < walker_begin || walker_end > S.k)
+    return set_error(h, NS_EINVAL, "walker range must lie in [0, num_delete = %d]", S.k);
+  if (ptr_kind != NS_PTR_HOST && ptr_kind != NS_PTR_DEVICE) return set_error(h, NS_EINVAL, "bad ptr_kind");
+  const size_t n = (size_t)(walker_end - walker_begin), D = S.D, j0 = (size_t)walker_begin;
+  if (n == 0) return NS_OK;
+  if (!u || !lnl || !n_accept || !n_like || !n_bins || !n_spec) return set_error(h, NS_EINVAL, "null array");
+  const cudaMemcpyKind kind = write ? (ptr_kind == NS_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice)
+                                    : (ptr_kind == NS_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice);
+  struct Part { void* dev; void* user; size_t bytes; };
+  const Part parts[6] = {{S.w_uo + j0 * D, u, sizeof(double) * n * D},
+                         {S.w_lo + j0, lnl, sizeof(double) * n},
+                         {S.w_na + j0, n_accept, sizeof(int32_t) * n},
+                         {S.w_nl + j0, n_like, sizeof(int32_t) * n},
+                         {S.w_nb + j0, n_bins, sizeof(int64_t) * n},
+                         {S.w_ns + j0, n_spec, sizeof(int64_t) * n}};
+  cudaError_t e = cudaSuccess;
+  for (const Part& p : parts) {
+    e = write ? cudaMemcpyAsync(p.dev, p.user, p.bytes, kind, h->stream)
+              : cudaMemcpyAsync(p.user, p.dev, p.bytes, kind, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "walk output copy");
+  }
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "walk output copy");
+  return NS_OK;
+}
+
+extern "C" int ns_batch_end(ns_handle* h, ns_progress* progress) {
+  int r = batch_checks(h, true);
+  if (r) return r;
+  const int ne = (int)h->events.size();
+  insert_kernel<<<ne, kSelThreads, 0, h->stream>>>(h->d_ns, h->d_tasks);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "insert launch");
+  h->kernel_launches += 1;
+  h->batch_open = false;
+  if ((r = download_states(h))) return r;
+  if (progress) fill_progress(h, progress);
+  for (auto& S : h->host_ns)
+    if (S.overflow) return set_error(h, NS_ENOMEM, "dead-point store overflow");
+  for (size_t ev = 0; ev < h->host_ns.size(); ++ev)
+    if (h->host_ns[ev].chol_bad)
+      return set_error(h, NS_EINVAL, "event %zu: the survivors' covariance is not positive definite (HRSS)", ev);
+  if ((r = watchdog_report(h))) return r;
+  bool warn = false;
+  for (auto& S : h->host_ns) warn = warn || S.zero_accept;
+  return warn ? NS_WMAXMCMC : NS_OK;
 }

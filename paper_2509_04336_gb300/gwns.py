@@ -69,8 +69,8 @@ class ns_progress(C.Structure):
 EXPORTS = ("ns_init", "ns_waveform", "ns_likelihood_batch", "ns_walk_batch", "ns_step", "ns_evidence",
            "ns_posterior", "ns_state_save", "ns_state_load", "ns_walk_batch_noalloc", "ns_flow_num_params",
            "ns_flow_set", "ns_flow_get", "ns_flow_logq", "ns_flow_sample", "ns_flow_grad", "ns_flow_train",
-           "ns_relbin_set", "ns_relbin_edges", "ns_hrss_batch", "ns_set_watchdog", "ns_set_abort", "ns_free",
-           "ns_last_error")
+           "ns_relbin_set", "ns_relbin_edges", "ns_hrss_batch", "ns_set_watchdog", "ns_set_abort",
+           "ns_batch_begin", "ns_batch_walk", "ns_batch_walk_io", "ns_batch_end", "ns_free", "ns_last_error")
 
 _lib = None
 
@@ -107,6 +107,10 @@ def load(path: str = LIB_PATH):
     lib.ns_hrss_batch.argtypes = [P, I, P, I, P, P, D, I, I, C.c_int64, C.c_int64, P, P, P, P]
     lib.ns_set_watchdog.argtypes = [P, D]
     lib.ns_set_abort.argtypes = [P, I]
+    lib.ns_batch_begin.argtypes = [P]
+    lib.ns_batch_walk.argtypes = [P, C.c_int64, C.c_int64]
+    lib.ns_batch_walk_io.argtypes = [P, I, C.c_int64, C.c_int64, P, P, P, P, P, P, I, I]
+    lib.ns_batch_end.argtypes = [P, C.POINTER(ns_progress)]
     lib.ns_free.argtypes = [P]
     lib.ns_free.restype = None
     lib.ns_last_error.argtypes = [P]
@@ -397,6 +401,29 @@ def ns_set_watchdog(h, budget_seconds: float):
 
 def ns_set_abort(h, flag: bool):
     return _check(_lib.ns_set_abort(h, 1 if flag else 0), h)
+
+
+def ns_batch_begin(h):
+    return _check(_lib.ns_batch_begin(h), h)
+
+
+def ns_batch_walk(h, walker_begin: int, walker_end: int):
+    return _check(_lib.ns_batch_walk(h, int(walker_begin), int(walker_end)), h)
+
+
+def ns_batch_walk_io(h, event: int, walker_begin: int, u, lnl, n_accept, n_like, n_bins, n_spec, write: bool):
+    """Copy the walk outputs of walkers [walker_begin, walker_begin + len(lnl)) of one event out of
+    the handle (write False) or into it (write True); arrays host (numpy) or CUDA tensors."""
+    ps = _same_kind(u, lnl, n_accept, n_like, n_bins, n_spec)
+    n = lnl.shape[0]
+    return _check(_lib.ns_batch_walk_io(h, event, int(walker_begin), int(walker_begin) + n, ps[0][0], ps[1][0],
+                                        ps[2][0], ps[3][0], ps[4][0], ps[5][0], ps[0][1], 1 if write else 0), h)
+
+
+def ns_batch_end(h, n_events: int = 1):
+    prog = (ns_progress * n_events)()
+    code = _check(_lib.ns_batch_end(h, prog), h, allow_warning=True)
+    return code, [p.as_dict() for p in prog]
 
 
 def ns_free(h):
