@@ -71,7 +71,7 @@ def test_speculation_autotuner_choice_and_chain():
     # the cost structure (FP64, short likelihoods of < 1k active bins: 8); from iteration 64 a
     # tuning pass tries every FP64 candidate cap {1, 2, 4, 8} in mirrored order and keeps one of
     # them; the depth in force never exceeds the cap.  Any depth gives the chain of the one-step
-    # walk, so the tuned run equals a run at a fixed depth bit for bit.
+    # walk, so the tuned run visits the points of a run at a fixed depth.
     evs = small_events(synth.PREC_FP64)
     iters = 80
     def run(spec):
@@ -101,7 +101,9 @@ def test_speculation_autotuner_choice_and_chain():
     for e in range(len(evs)):
         assert prog_a[e]["iterations"] == prog_f[e]["iterations"] == iters
         assert prog_a[e]["n_like"] == prog_f[e]["n_like"]
-        assert prog_a[e]["log_z"] == prog_f[e]["log_z"]
+        # the same points; ln L can differ in its last bits (a round of fewer proposals than
+        # warps sums each on the whole CTA, a longer one on one warp each)
+        assert abs(prog_a[e]["log_z"] - prog_f[e]["log_z"]) <= 1e-12 * abs(prog_f[e]["log_z"])
         assert np.array_equal(post_a[e][0], post_f[e][0])
 
 
