@@ -17,7 +17,7 @@ using namespace gwns;
 
 namespace {
 
-constexpr int kTilesCap = (kMaxLive + 127) / 128;
+constexpr int kTilesCap = (kMaxLive + kGradRows - 1) / kGradRows;
 
 __global__ void flow_train_flag_kernel(const NsState* S, int every, int32_t* flag) {
   if (threadIdx.x == 0) *flag = (!S->done && S->iteration % every == 0) ? 1 : 0;
@@ -388,7 +388,7 @@ static int flow_points_upload(ns_handle* h, const EventHost& E, const double* u,
 }
 
 static int loss_sum(ns_handle* h, const FlowHost& Fh, int n, cudaStream_t s, double* loss) {
-  std::vector<double> lp((n + 127) / 128);
+  std::vector<double> lp((n + kGradRows - 1) / kGradRows);
   cudaError_t e = cudaMemcpyAsync(lp.data(), Fh.d_loss_part, sizeof(double) * lp.size(), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "flow loss");

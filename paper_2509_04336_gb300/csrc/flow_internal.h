@@ -9,6 +9,11 @@
 
 namespace gwns {
 
+// Points per tile of the flow gradient: a tile fills the top half of the 128-row MMA operands (the
+// rest are masked rows), so that twice as many CTAs share the survivors -- the kernel is bound by
+// its per-layer latency, not by the tensor pipe.
+constexpr int kGradRows = 64;
+
 // Device buffers of one event's flow (all owned by the handle).
 struct FlowHost {
   int enabled = 0;

@@ -385,8 +385,8 @@ __global__ void __launch_bounds__(kFT, 1) flow_grad_kernel(GradArgs G) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int D = F.n_dim, L = F.n_layers, NP = F.n_params, LP = flow_layer_params(D);
   const int tile = blockIdx.x;
-  const int row = tile * kFT + tid;
-  const bool valid = row < G.n;
+  const int row = tile * kGradRows + tid;
+  const bool valid = tid < kGradRows && row < G.n;
   if (G.bump_t && tile == 0 && tid == 0) F.adam_t += 1;
 
   unsigned char *XA = sm + kGrXA, *HA = sm + kGrHA, *HB = sm + kGrHB, *G3 = sm + kGrG3;
@@ -956,15 +956,15 @@ cudaError_t launch_flow_grad(FlowDev* d_flow, const double* d_u, int n, const in
                              float* d_partial, double* d_loss_part, float* d_zsave, int32_t* d_err, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   GradArgs G{d_flow, d_u, n, d_active, bump_t, d_partial, d_loss_part, d_zsave, d_err};
-  flow_grad_kernel<<<(n + kFT - 1) / kFT, kFT, kGrBytes, s>>>(G);
+  flow_grad_kernel<<<(n + kGradRows - 1) / kGradRows, kFT, kGrBytes, s>>>(G);
   return cudaGetLastError();
 }
 
 cudaError_t launch_flow_adam(FlowDev* d_flow, unsigned char* d_img, float* d_bias, float* d_master, float* d_m,
                              float* d_v, const float* d_partial, int n, const int32_t* d_active, float* d_grad_out,
                              int n_params, cudaStream_t s) {
-  AdamArgs A{d_flow, d_img, d_bias, d_master, d_m, d_v, d_partial, (n + kFT - 1) / kFT, 1.0f / (float)n, d_active,
-             d_grad_out};
+  AdamArgs A{d_flow, d_img, d_bias, d_master, d_m, d_v, d_partial, (n + kGradRows - 1) / kGradRows, 1.0f / (float)n,
+             d_active, d_grad_out};
   const int blocks = (n_params + 255) / 256;
   flow_adam_kernel<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(A);
   return cudaGetLastError();
