@@ -196,14 +196,14 @@ static int prepare_event(ns_handle* h, int e, const ns_config& c, const ns_event
       (err = cudaMalloc(&E.d_gw32, gw32.size() * sizeof(float))) != cudaSuccess ||
       (err = cudaMalloc(&E.d_hhp32, pref32.size() * sizeof(float))) != cudaSuccess)
     return set_error(nullptr, NS_ENOMEM, "event %d: device allocation failed: %s", e, cudaGetErrorString(err));
-  if ((err = cudaMemcpy(E.d_basis64, basis.data(), basis.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (err = cudaMemcpy(E.d_basis_ff, basis_ff.data(), basis_ff.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (err = cudaMemcpy(E.d_z64, z64.data(), z64.size() * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (err = cudaMemcpy(E.d_z32, z32.data(), z32.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (err = cudaMemcpy(E.d_hh_prefix, pref.data(), pref.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (err = cudaMemcpy(E.d_gw64, gw64.data(), gw64.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (err = cudaMemcpy(E.d_gw32, gw32.data(), gw32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (err = cudaMemcpy(E.d_hhp32, pref32.data(), pref32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((err = copy_on(h, E.d_basis64, basis.data(), basis.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = copy_on(h, E.d_basis_ff, basis_ff.data(), basis_ff.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = copy_on(h, E.d_z64, z64.data(), z64.size() * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = copy_on(h, E.d_z32, z32.data(), z32.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = copy_on(h, E.d_hh_prefix, pref.data(), pref.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = copy_on(h, E.d_gw64, gw64.data(), gw64.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = copy_on(h, E.d_gw32, gw32.data(), gw32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = copy_on(h, E.d_hhp32, pref32.data(), pref32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
     return set_error(nullptr, NS_ECUDA, "event %d: upload failed: %s", e, cudaGetErrorString(err));
 
   EventDev& D = E.dev;
@@ -353,9 +353,9 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
   }
   std::vector<EventDev> tab(n_events);
   for (int e = 0; e < n_events; ++e) tab[e] = h->events[e].dev;
-  if ((e0 = cudaMemcpy(h->d_events, tab.data(), sizeof(EventDev) * n_events, cudaMemcpyHostToDevice)) != cudaSuccess ||
+  if ((e0 = copy_on(h, h->d_events, tab.data(), sizeof(EventDev) * n_events, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e0 = cudaMalloc(&h->d_status, sizeof(int32_t) * 4)) != cudaSuccess ||
-      (e0 = cudaMemset(h->d_status, 0, sizeof(int32_t) * 4)) != cudaSuccess) {
+      (e0 = fill_on(h, h->d_status, 0, sizeof(int32_t) * 4)) != cudaSuccess) {
     ns_free(h);
     return set_error(nullptr, NS_ECUDA, "event table upload: %s", cudaGetErrorString(e0));
   }
@@ -557,10 +557,22 @@ void watchdog_fields(ns_handle* h, WalkTask& T) {
   T.budget_ns = h->budget_ns;
 }
 
+cudaError_t copy_on(ns_handle* h, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  if (bytes == 0) return cudaSuccess;
+  const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, h->stream);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(h->stream);
+}
+
+cudaError_t fill_on(ns_handle* h, void* dst, int value, size_t bytes) {
+  if (bytes == 0) return cudaSuccess;
+  const cudaError_t e = cudaMemsetAsync(dst, value, bytes, h->stream);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(h->stream);
+}
+
 // NS_ETIMEOUT when a walk of the handle stopped on its watchdog since the bit was last cleared.
 int watchdog_report(ns_handle* h) {
   int32_t st = 0;
-  cudaError_t e = cudaMemcpy(&st, h->d_status + 2, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaError_t e = copy_on(h, &st, h->d_status + 2, sizeof(int32_t), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(h, e, "watchdog status");
   if (st) return set_error(h, NS_ETIMEOUT, "a walk stopped on the watchdog (time budget or abort flag)");
   return NS_OK;
@@ -574,9 +586,9 @@ extern "C" int ns_set_watchdog(ns_handle* h, double budget_seconds) {
   h->budget_ns = (uint64_t)(budget_seconds * 1e9);
   if (budget_seconds > 0.0 && h->budget_ns == 0) h->budget_ns = 1;
   // the sampler's tasks read it at every batch
-  cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaError_t e = cudaSuccess;
   for (size_t ev = 0; ev < h->events.size() && e == cudaSuccess && h->d_tasks; ++ev)
-    e = cudaMemcpy(&h->d_tasks[ev].budget_ns, &h->budget_ns, sizeof(uint64_t), cudaMemcpyHostToDevice);
+    e = copy_on(h, &h->d_tasks[ev].budget_ns, &h->budget_ns, sizeof(uint64_t), cudaMemcpyHostToDevice);
   return e == cudaSuccess ? NS_OK : cuda_fail(h, e, "watchdog budget");
 }
 

@@ -113,6 +113,12 @@ int set_error(ns_handle* h, int code, const char* fmt, ...);
 void watchdog_fields(ns_handle* h, gwns::WalkTask& T);
 int watchdog_report(ns_handle* h);
 int cuda_fail(ns_handle* h, cudaError_t e, const char* what);
+// A copy (fill) ordered on the handle's stream -- after the work enqueued there, before the work
+// enqueued later -- and complete on return.  The handle's stream is non-blocking, so a plain
+// cudaMemcpy / cudaMemset (legacy default stream) is ordered with neither, and it returns before
+// a device-to-device copy, a fill or the DMA of a host-to-device copy has landed.
+cudaError_t copy_on(ns_handle* h, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind);
+cudaError_t fill_on(ns_handle* h, void* dst, int value, size_t bytes);
 int ensure_scratch(ns_handle* h, gwns::Scratch& s, size_t bytes);
 int nested_init(ns_handle* h);
 int default_spec(int precision);

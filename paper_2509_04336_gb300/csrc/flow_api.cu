@@ -118,11 +118,11 @@ int flow_setup(ns_handle* h, int e) {
       (r = falloc(h, (void**)&Fh.d_tab_lq, sizeof(double) * k * Fh.stride, "flow proposal table")) ||
       (r = falloc(h, (void**)&Fh.d_train, sizeof(int32_t), "flow flag")))
     return r;
-  if ((err = cudaMemset(Fh.d_img, 0, L * kImgLayer)) != cudaSuccess ||
-      (err = cudaMemset(Fh.d_bias, 0, sizeof(float) * L * kBiasLayer)) != cudaSuccess)
+  if ((err = fill_on(h, Fh.d_img, 0, L * kImgLayer)) != cudaSuccess ||
+      (err = fill_on(h, Fh.d_bias, 0, sizeof(float) * L * kBiasLayer)) != cudaSuccess)
     return cuda_fail(h, err, "flow image clear");
   FlowDev F = host_flowdev(E);
-  if ((err = cudaMemcpy(Fh.d_flow, &F, sizeof(F), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((err = copy_on(h, Fh.d_flow, &F, sizeof(F), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(h, err, "flow upload");
   if ((err = launch_flow_init(Fh.d_flow, Fh.d_master, Fh.d_m, Fh.d_v, (int)NP, c.seed, (uint64_t)e, h->stream)) ||
       (err = launch_flow_pack(Fh.d_flow, Fh.d_img, Fh.d_bias, Fh.d_master, (int)NP, h->stream)) ||
@@ -221,10 +221,10 @@ bool flow_state_write(ns_handle* h, int e, FILE* f) {
   if (!Fh.enabled) return true;
   FlowDev F;
   std::vector<float> buf((size_t)Fh.n_params * 3);
-  if (cudaMemcpy(&F, Fh.d_flow, sizeof(F), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(buf.data(), Fh.d_master, sizeof(float) * Fh.n_params, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(buf.data() + Fh.n_params, Fh.d_m, sizeof(float) * Fh.n_params, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(buf.data() + 2 * (size_t)Fh.n_params, Fh.d_v, sizeof(float) * Fh.n_params, cudaMemcpyDeviceToHost) !=
+  if (copy_on(h, &F, Fh.d_flow, sizeof(F), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      copy_on(h, buf.data(), Fh.d_master, sizeof(float) * Fh.n_params, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      copy_on(h, buf.data() + Fh.n_params, Fh.d_m, sizeof(float) * Fh.n_params, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      copy_on(h, buf.data() + 2 * (size_t)Fh.n_params, Fh.d_v, sizeof(float) * Fh.n_params, cudaMemcpyDeviceToHost) !=
           cudaSuccess)
     return false;
   return fwrite(&F, sizeof(F), 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
@@ -251,10 +251,10 @@ bool flow_state_apply(ns_handle* h, int e, const FlowBlob& b) {
   cur.log_sigma_sum = b.F.log_sigma_sum;
   cur.adam_t = b.F.adam_t;
   const float* buf = b.buf.data();
-  return cudaMemcpy(Fh.d_flow, &cur, sizeof(cur), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(Fh.d_master, buf, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(Fh.d_m, buf + Fh.n_params, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(Fh.d_v, buf + 2 * (size_t)Fh.n_params, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) ==
+  return copy_on(h, Fh.d_flow, &cur, sizeof(cur), cudaMemcpyHostToDevice) == cudaSuccess &&
+         copy_on(h, Fh.d_master, buf, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) == cudaSuccess &&
+         copy_on(h, Fh.d_m, buf + Fh.n_params, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) == cudaSuccess &&
+         copy_on(h, Fh.d_v, buf + 2 * (size_t)Fh.n_params, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice) ==
              cudaSuccess &&
          launch_flow_pack(Fh.d_flow, Fh.d_img, Fh.d_bias, Fh.d_master, Fh.n_params, h->stream) == cudaSuccess &&
          cudaStreamSynchronize(h->stream) == cudaSuccess;
@@ -289,10 +289,10 @@ extern "C" int ns_flow_set(ns_handle* h, int event, const float* params, const d
   F.log_sigma_sum = lss;
   cudaError_t e;
   if ((e = cudaStreamSynchronize(h->stream)) ||
-      (e = cudaMemcpy(Fh.d_flow, &F, sizeof(F), cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(Fh.d_master, params, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemset(Fh.d_m, 0, sizeof(float) * Fh.n_params)) ||
-      (e = cudaMemset(Fh.d_v, 0, sizeof(float) * Fh.n_params)) ||
+      (e = copy_on(h, Fh.d_flow, &F, sizeof(F), cudaMemcpyHostToDevice)) ||
+      (e = copy_on(h, Fh.d_master, params, sizeof(float) * Fh.n_params, cudaMemcpyHostToDevice)) ||
+      (e = fill_on(h, Fh.d_m, 0, sizeof(float) * Fh.n_params)) ||
+      (e = fill_on(h, Fh.d_v, 0, sizeof(float) * Fh.n_params)) ||
       (e = launch_flow_pack(Fh.d_flow, Fh.d_img, Fh.d_bias, Fh.d_master, Fh.n_params, h->stream)) ||
       (e = cudaStreamSynchronize(h->stream)))
     return cuda_fail(h, e, "flow set");
@@ -306,9 +306,9 @@ extern "C" int ns_flow_get(ns_handle* h, int event, float* params, double* mu, d
   FlowHost& Fh = E.flow;
   FlowDev F;
   cudaError_t e;
-  if ((e = cudaStreamSynchronize(h->stream)) || (e = cudaMemcpy(&F, Fh.d_flow, sizeof(F), cudaMemcpyDeviceToHost)))
+  if ((e = cudaStreamSynchronize(h->stream)) || (e = copy_on(h, &F, Fh.d_flow, sizeof(F), cudaMemcpyDeviceToHost)))
     return cuda_fail(h, e, "flow get");
-  if (params && (e = cudaMemcpy(params, Fh.d_master, sizeof(float) * Fh.n_params, cudaMemcpyDeviceToHost)))
+  if (params && (e = copy_on(h, params, Fh.d_master, sizeof(float) * Fh.n_params, cudaMemcpyDeviceToHost)))
     return cuda_fail(h, e, "flow get");
   for (int d = 0; d < E.n_dim; ++d) {
     if (mu) mu[d] = F.mu[d];

@@ -393,7 +393,7 @@ double batch_delay(double delay, int k) {
 int upload_states(ns_handle* h) {
   std::vector<NsState> st;
   for (auto& E : h->events) st.push_back(E.ns);
-  cudaError_t e = cudaMemcpy(h->d_ns, st.data(), sizeof(NsState) * st.size(), cudaMemcpyHostToDevice);
+  cudaError_t e = copy_on(h, h->d_ns, st.data(), sizeof(NsState) * st.size(), cudaMemcpyHostToDevice);
   return e == cudaSuccess ? NS_OK : cuda_fail(h, e, "state upload");
 }
 
@@ -424,10 +424,10 @@ int grow_dead(ns_handle* h, int e, int64_t need, int64_t rows) {
   size_t nd = (size_t)rows;
   cudaError_t err = cudaSuccess;
   if (nd) {
-    if ((err = cudaMemcpy(du, S.dead_u, sizeof(double) * nd * S.D, cudaMemcpyDeviceToDevice)) ||
-        (err = cudaMemcpy(dl, S.dead_lnl, sizeof(double) * nd, cudaMemcpyDeviceToDevice)) ||
-        (err = cudaMemcpy(dw, S.dead_logw, sizeof(double) * nd, cudaMemcpyDeviceToDevice)) ||
-        (err = cudaMemcpy(dn, S.dead_nlive, sizeof(int32_t) * nd, cudaMemcpyDeviceToDevice)))
+    if ((err = copy_on(h, du, S.dead_u, sizeof(double) * nd * S.D, cudaMemcpyDeviceToDevice)) ||
+        (err = copy_on(h, dl, S.dead_lnl, sizeof(double) * nd, cudaMemcpyDeviceToDevice)) ||
+        (err = copy_on(h, dw, S.dead_logw, sizeof(double) * nd, cudaMemcpyDeviceToDevice)) ||
+        (err = copy_on(h, dn, S.dead_nlive, sizeof(int32_t) * nd, cudaMemcpyDeviceToDevice)))
       return cuda_fail(h, err, "dead store copy");
   }
   cudaFree(S.dead_u); cudaFree(S.dead_lnl); cudaFree(S.dead_logw); cudaFree(S.dead_nlive);
@@ -435,11 +435,11 @@ int grow_dead(ns_handle* h, int e, int64_t need, int64_t rows) {
   S.dead_cap = cap;
   // patch the pointer and capacity fields of the device state
   NsState* d = h->d_ns + e;
-  if ((err = cudaMemcpy(&d->dead_cap, &S.dead_cap, sizeof(int64_t), cudaMemcpyHostToDevice)) ||
-      (err = cudaMemcpy(&d->dead_u, &S.dead_u, sizeof(double*), cudaMemcpyHostToDevice)) ||
-      (err = cudaMemcpy(&d->dead_lnl, &S.dead_lnl, sizeof(double*), cudaMemcpyHostToDevice)) ||
-      (err = cudaMemcpy(&d->dead_logw, &S.dead_logw, sizeof(double*), cudaMemcpyHostToDevice)) ||
-      (err = cudaMemcpy(&d->dead_nlive, &S.dead_nlive, sizeof(int32_t*), cudaMemcpyHostToDevice)))
+  if ((err = copy_on(h, &d->dead_cap, &S.dead_cap, sizeof(int64_t), cudaMemcpyHostToDevice)) ||
+      (err = copy_on(h, &d->dead_u, &S.dead_u, sizeof(double*), cudaMemcpyHostToDevice)) ||
+      (err = copy_on(h, &d->dead_lnl, &S.dead_lnl, sizeof(double*), cudaMemcpyHostToDevice)) ||
+      (err = copy_on(h, &d->dead_logw, &S.dead_logw, sizeof(double*), cudaMemcpyHostToDevice)) ||
+      (err = copy_on(h, &d->dead_nlive, &S.dead_nlive, sizeof(int32_t*), cudaMemcpyHostToDevice)))
     return cuda_fail(h, err, "dead store patch");
   return NS_OK;
 }
@@ -591,9 +591,9 @@ int nested_init(ns_handle* h) {
     for (int j = 0; j < h->events[e].ns.k; ++j) { bt.push_back(e); bl.push_back(j); }
   h->n_walk_blocks = total_walkers;
   cudaError_t err;
-  if ((err = cudaMemcpy(h->d_tasks, tasks.data(), sizeof(WalkTask) * ne, cudaMemcpyHostToDevice)) ||
-      (err = cudaMemcpy(h->d_blk_task, bt.data(), sizeof(int32_t) * bt.size(), cudaMemcpyHostToDevice)) ||
-      (err = cudaMemcpy(h->d_blk_local, bl.data(), sizeof(int32_t) * bl.size(), cudaMemcpyHostToDevice)))
+  if ((err = copy_on(h, h->d_tasks, tasks.data(), sizeof(WalkTask) * ne, cudaMemcpyHostToDevice)) ||
+      (err = copy_on(h, h->d_blk_task, bt.data(), sizeof(int32_t) * bt.size(), cudaMemcpyHostToDevice)) ||
+      (err = copy_on(h, h->d_blk_local, bl.data(), sizeof(int32_t) * bl.size(), cudaMemcpyHostToDevice)))
     return cuda_fail(h, err, "task upload");
   if ((r = upload_states(h))) return r;
   // initial live points and their likelihoods (Sec. 2.2.1)
@@ -666,9 +666,9 @@ int set_spec_cap(ns_handle* h, int cap) {
     const int32_t spec = S.spec_rule < cap ? S.spec_rule : cap;
     NsState* d = h->d_ns + e;
     cudaError_t err;
-    if ((err = cudaMemcpy(&d->spec_cap, &cap, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
-        (err = cudaMemcpy(&d->spec, &spec, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
-        (err = cudaMemcpy(&h->d_tasks[e].spec, &spec, sizeof(int32_t), cudaMemcpyHostToDevice)))
+    if ((err = copy_on(h, &d->spec_cap, &cap, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+        (err = copy_on(h, &d->spec, &spec, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+        (err = copy_on(h, &h->d_tasks[e].spec, &spec, sizeof(int32_t), cudaMemcpyHostToDevice)))
       return cuda_fail(h, err, "speculation cap");
   }
   return NS_OK;
@@ -789,9 +789,9 @@ extern "C" int ns_evidence(ns_handle* h, int event, double* log_z, double* log_z
   const int64_t nd = S.n_dead;
   std::vector<double> dl(nd), dw(nd), ll(S.n_live);
   cudaError_t e;
-  if ((e = cudaMemcpy(dl.data(), S.dead_lnl, sizeof(double) * nd, cudaMemcpyDeviceToHost)) ||
-      (e = cudaMemcpy(dw.data(), S.dead_logw, sizeof(double) * nd, cudaMemcpyDeviceToHost)) ||
-      (e = cudaMemcpy(ll.data(), S.live_lnl, sizeof(double) * S.n_live, cudaMemcpyDeviceToHost)))
+  if ((e = copy_on(h, dl.data(), S.dead_lnl, sizeof(double) * nd, cudaMemcpyDeviceToHost)) ||
+      (e = copy_on(h, dw.data(), S.dead_logw, sizeof(double) * nd, cudaMemcpyDeviceToHost)) ||
+      (e = copy_on(h, ll.data(), S.live_lnl, sizeof(double) * S.n_live, cudaMemcpyDeviceToHost)))
     return cuda_fail(h, e, "evidence download");
   // ln Z = logsumexp(dead ln w, live ln L + ln X - ln n), in FP64
   double m = -INFINITY;
@@ -847,15 +847,15 @@ extern "C" int ns_posterior(ns_handle* h, int event, double* theta_out, double* 
   if ((r = alloc(h, (void**)&d_u, sizeof(double) * m * D, "posterior u"))) return r;
   if ((r = alloc(h, (void**)&d_th, sizeof(double) * m * kParams, "posterior theta"))) { cudaFree(d_u); return r; }
   const int64_t from_dead = m < S.n_dead ? m : S.n_dead;
-  cudaError_t e = cudaMemcpy(d_u, S.dead_u, sizeof(double) * from_dead * D, cudaMemcpyDeviceToDevice);
+  cudaError_t e = copy_on(h, d_u, S.dead_u, sizeof(double) * from_dead * D, cudaMemcpyDeviceToDevice);
   if (e == cudaSuccess && m > from_dead)
-    e = cudaMemcpy(d_u + from_dead * D, S.live_u, sizeof(double) * (m - from_dead) * D, cudaMemcpyDeviceToDevice);
+    e = copy_on(h, d_u + from_dead * D, S.live_u, sizeof(double) * (m - from_dead) * D, cudaMemcpyDeviceToDevice);
   if (e == cudaSuccess) e = launch_unit_to_theta(h->d_events + event, d_u, m, d_th, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e == cudaSuccess) e = cudaMemcpy(theta_out, d_th, sizeof(double) * m * kParams, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = copy_on(h, theta_out, d_th, sizeof(double) * m * kParams, cudaMemcpyDeviceToHost);
   std::vector<double> dw(from_dead), ll(S.n_live);
-  if (e == cudaSuccess) e = cudaMemcpy(dw.data(), S.dead_logw, sizeof(double) * from_dead, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(ll.data(), S.live_lnl, sizeof(double) * S.n_live, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = copy_on(h, dw.data(), S.dead_logw, sizeof(double) * from_dead, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = copy_on(h, ll.data(), S.live_lnl, sizeof(double) * S.n_live, cudaMemcpyDeviceToHost);
   cudaFree(d_u);
   cudaFree(d_th);
   if (e != cudaSuccess) return cuda_fail(h, e, "posterior");
@@ -873,16 +873,10 @@ bool wr(FILE* f, const void* p, size_t n) { return fwrite(p, 1, n, f) == n; }
 bool rd(FILE* f, void* p, size_t n) { return fread(p, 1, n, f) == n; }
 
 template <class T>
-bool dev_write(FILE* f, const T* d, size_t n) {
+bool dev_write(ns_handle* h, FILE* f, const T* d, size_t n) {
   std::vector<T> v(n);
-  if (n && cudaMemcpy(v.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  if (n && copy_on(h, v.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
   return wr(f, v.data(), sizeof(T) * n);
-}
-template <class T>
-bool dev_read(FILE* f, T* d, size_t n) {
-  std::vector<T> v(n);
-  if (!rd(f, v.data(), sizeof(T) * n)) return false;
-  return !n || cudaMemcpy(d, v.data(), sizeof(T) * n, cudaMemcpyHostToDevice) == cudaSuccess;
 }
 }  // namespace
 
@@ -900,9 +894,9 @@ extern "C" int ns_state_save(ns_handle* h, const char* path) {
   for (int e = 0; e < ne && ok; ++e) {
     const NsState& S = h->host_ns[e];
     ok = ok && wr(f, &S, sizeof(S));
-    ok = ok && dev_write(f, S.live_u, (size_t)S.n_live * S.D) && dev_write(f, S.live_lnl, (size_t)S.n_live);
-    ok = ok && dev_write(f, S.dead_u, (size_t)S.n_dead * S.D) && dev_write(f, S.dead_lnl, (size_t)S.n_dead);
-    ok = ok && dev_write(f, S.dead_logw, (size_t)S.n_dead) && dev_write(f, S.dead_nlive, (size_t)S.n_dead);
+    ok = ok && dev_write(h, f, S.live_u, (size_t)S.n_live * S.D) && dev_write(h, f, S.live_lnl, (size_t)S.n_live);
+    ok = ok && dev_write(h, f, S.dead_u, (size_t)S.n_dead * S.D) && dev_write(h, f, S.dead_lnl, (size_t)S.n_dead);
+    ok = ok && dev_write(h, f, S.dead_logw, (size_t)S.n_dead) && dev_write(h, f, S.dead_nlive, (size_t)S.n_dead);
     ok = ok && flow_state_write(h, e, f);
   }
   ok = (fclose(f) == 0) && ok;
@@ -951,12 +945,12 @@ extern "C" int ns_state_load(ns_handle* h, const char* path) {
     EventHost& E = h->events[e];
     const size_t nl = (size_t)R.S.n_live, nd = (size_t)R.S.n_dead, D = (size_t)R.S.D;
     cudaError_t err;
-    if ((err = cudaMemcpy(E.ns.live_u, R.live_u.data(), sizeof(double) * nl * D, cudaMemcpyHostToDevice)) ||
-        (err = cudaMemcpy(E.ns.live_lnl, R.live_lnl.data(), sizeof(double) * nl, cudaMemcpyHostToDevice)) ||
-        (nd && (err = cudaMemcpy(E.ns.dead_u, R.dead_u.data(), sizeof(double) * nd * D, cudaMemcpyHostToDevice))) ||
-        (nd && (err = cudaMemcpy(E.ns.dead_lnl, R.dead_lnl.data(), sizeof(double) * nd, cudaMemcpyHostToDevice))) ||
-        (nd && (err = cudaMemcpy(E.ns.dead_logw, R.dead_logw.data(), sizeof(double) * nd, cudaMemcpyHostToDevice))) ||
-        (nd && (err = cudaMemcpy(E.ns.dead_nlive, R.dead_nlive.data(), sizeof(int32_t) * nd, cudaMemcpyHostToDevice))))
+    if ((err = copy_on(h, E.ns.live_u, R.live_u.data(), sizeof(double) * nl * D, cudaMemcpyHostToDevice)) ||
+        (err = copy_on(h, E.ns.live_lnl, R.live_lnl.data(), sizeof(double) * nl, cudaMemcpyHostToDevice)) ||
+        (nd && (err = copy_on(h, E.ns.dead_u, R.dead_u.data(), sizeof(double) * nd * D, cudaMemcpyHostToDevice))) ||
+        (nd && (err = copy_on(h, E.ns.dead_lnl, R.dead_lnl.data(), sizeof(double) * nd, cudaMemcpyHostToDevice))) ||
+        (nd && (err = copy_on(h, E.ns.dead_logw, R.dead_logw.data(), sizeof(double) * nd, cudaMemcpyHostToDevice))) ||
+        (nd && (err = copy_on(h, E.ns.dead_nlive, R.dead_nlive.data(), sizeof(int32_t) * nd, cudaMemcpyHostToDevice))))
       return cuda_fail(h, err, "state upload");
     if (!flow_state_apply(h, e, R.flow)) return set_error(h, NS_ECUDA, "flow state upload failed");
     // the checkpoint's scalar state (every field before the buffer pointers); this handle keeps
@@ -965,10 +959,10 @@ extern "C" int ns_state_load(ns_handle* h, const char* path) {
     std::memcpy(&S, &R.S, offsetof(NsState, live_u));
     S.dead_cap = E.ns.dead_cap;
     WalkTask* dt = h->d_tasks + e;
-    if ((err = cudaMemcpy(h->d_ns + e, &S, sizeof(S), cudaMemcpyHostToDevice)) ||
-        (err = cudaMemcpy(&dt->done, &S.done, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
-        (err = cudaMemcpy(&dt->n_steps, &S.n_steps, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
-        (err = cudaMemcpy(&dt->spec, &S.spec, sizeof(int32_t), cudaMemcpyHostToDevice)))
+    if ((err = copy_on(h, h->d_ns + e, &S, sizeof(S), cudaMemcpyHostToDevice)) ||
+        (err = copy_on(h, &dt->done, &S.done, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+        (err = copy_on(h, &dt->n_steps, &S.n_steps, sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+        (err = copy_on(h, &dt->spec, &S.spec, sizeof(int32_t), cudaMemcpyHostToDevice)))
       return cuda_fail(h, err, "state upload");
   }
   return download_states(h);

@@ -45,7 +45,7 @@ void relbin_free(EventHost& E) {
 static int relbin_adopt(ns_handle* h, int event, const EventDev& nd, int32_t* ed, float2* q0, float2* a, float4* b) {
   EventHost& E = h->events[event];
   cudaError_t e;
-  if ((e = cudaMemcpy(h->d_events + event, &nd, sizeof(EventDev), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = copy_on(h, h->d_events + event, &nd, sizeof(EventDev), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(h, e, "event upload");
   relbin_free(E);
   E.dev = nd;
@@ -216,10 +216,10 @@ extern "C" int ns_relbin_set(ns_handle* h, int event, const int32_t* edges, int 
     drop();
     return set_error(h, NS_ENOMEM, "relative-binning allocation failed: %s", cudaGetErrorString(e));
   }
-  if ((e = cudaMemcpy(ned, edges, sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(nq0, q0.data(), sizeof(float2) * q0.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(na, a.data(), sizeof(float2) * a.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(nbb, b.data(), sizeof(float4) * b.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+  if ((e = copy_on(h, ned, edges, sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = copy_on(h, nq0, q0.data(), sizeof(float2) * q0.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = copy_on(h, na, a.data(), sizeof(float2) * a.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = copy_on(h, nbb, b.data(), sizeof(float4) * b.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
     drop();
     return cuda_fail(h, e, "relative-binning upload");
   }
