@@ -119,25 +119,6 @@ __device__ __forceinline__ void warp_reduce_f64(double* dv) {
   }
 }
 
-template <int NV>
-__device__ __forceinline__ void warp_reduce_f32(float* fv, float* fc) {
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    float s = fv[i], c = fc[i];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      float so = __shfl_down_sync(0xffffffffu, s, off);
-      float co = __shfl_down_sync(0xffffffffu, c, off);
-      float t, e;
-      two_sum(s, so, t, e);
-      s = t;
-      c = c + co + e;
-    }
-    fv[i] = s;
-    fc[i] = c;
-  }
-}
-
 // Compensated all-lane sums of NV values by recursive halving: at the exchange with offset
 // S each lane keeps half of the values it still carries (the upper half when bit S of its
 // lane is set) and adds its partner's copy of that half, so V = NV rounded up to a power of
@@ -197,29 +178,104 @@ __device__ __forceinline__ void warp_halving_sums(const float* fv, const float* 
   index = idx;
 }
 
-// Sums of one walker over the whole CTA (stride kThreads), totals in `out` for thread 0.
+// The same halving in FP64 (plain additions): lane l ends with the total of value index
+// vbits(l), as above.
+template <int V, int S>
+__device__ __forceinline__ void halve_step_f64(double* s, int lane) {
+  const bool up = (lane & S) != 0;
+#pragma unroll
+  for (int i = 0; i < V / 2; ++i) {
+    const double send = up ? s[i] : s[i + V / 2], keep = up ? s[i + V / 2] : s[i];
+    s[i] = keep + __shfl_xor_sync(0xffffffffu, send, S);
+  }
+}
+template <int S>
+__device__ __forceinline__ void fold_step_f64(double& s) {
+  s = s + __shfl_xor_sync(0xffffffffu, s, S);
+}
+template <int NV>
+__device__ __forceinline__ void warp_halving_f64(const double* dv, int lane, double& out, int& index) {
+  constexpr int V = Pow2Vals<NV>::value;
+  double s[V];
+#pragma unroll
+  for (int i = 0; i < V; ++i) s[i] = i < NV ? dv[i] : 0.0;
+  halve_step_f64<V, 16>(s, lane);
+  if (V >= 4) halve_step_f64<V / 2, 8>(s, lane);
+  if (V >= 8) halve_step_f64<V / 4, 4>(s, lane);
+  if (V >= 16) halve_step_f64<V / 8, 2>(s, lane);
+  double r = s[0];
+  if (V <= 8) fold_step_f64<2>(r);
+  if (V <= 4) fold_step_f64<4>(r);
+  if (V <= 2) fold_step_f64<8>(r);
+  fold_step_f64<1>(r);
+  int idx = (lane >> 4) & 1;
+  if (V >= 4) idx = (idx << 1) | ((lane >> 3) & 1);
+  if (V >= 8) idx = (idx << 1) | ((lane >> 2) & 1);
+  if (V >= 16) idx = (idx << 1) | ((lane >> 1) & 1);
+  out = r;
+  index = idx;
+}
+
+// One proposal's sum has one order whichever threads evaluate it, so that its ln L does not
+// depend on the round it was drawn in or on the kernel that evaluates it: chunk w (w = 0..3) is
+// the bins 32 w + l + 128 m (m = 0, 1, ...) summed in order on lane l, the lanes' values are
+// reduced by the halving tree (compensated in the mixed paths, then converted to FP64), and
+// the four chunk totals are added in the order of w in FP64.  The whole CTA forms chunk w on
+// warp w; a warp that evaluates a proposal alone forms the four chunks in turn.
+//
+// chunk_total: this warp's chunk total of every value into out[0 .. NV) (shared memory).
+template <int PREC, int NV>
+__device__ __forceinline__ void chunk_total(const double* dv, const float* fv, const float* fc, int lane,
+                                            double* out) {
+  constexpr int group = 32 / Pow2Vals<NV>::value;
+  int q;
+  if (PREC == 0) {
+    double r;
+    warp_halving_f64<NV>(dv, lane, r, q);
+    if ((lane & (group - 1)) == 0 && q < NV) out[q] = r;
+  } else {
+    float rs, rc;
+    warp_halving_sums<NV>(fv, fc, lane, rs, rc, q);
+    if ((lane & (group - 1)) == 0 && q < NV) out[q] = (double)rs + (double)rc;
+  }
+}
+// value q of the four chunk totals ct[w][q], added in chunk order
+template <int NV>
+__device__ __forceinline__ double chunks_sum(const double (*ct)[NV], int q) {
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) t = t + ct[w][q];
+  return t;
+}
+// The four chunks of one proposal on one warp: totals into ct[0 .. kWarps)[0 .. NV).
 template <int PREC, int NDET, int WF>
-__device__ inline void cta_sums(const EventDev& ev, const WalkerParams& P, double (*red)[kMaxVals], double* out) {
+__device__ inline void warp_chunks(const EventDev& ev, const WalkerParams& P, int lane,
+                                   double (*ct)[NVals<NDET, WF>::value]) {
+  constexpr int NV = NVals<NDET, WF>::value;
+#pragma unroll 1
+  for (int w = 0; w < kWarps; ++w) {
+    double dv[NV];
+    float fv[NV], fc[NV];
+    partials<PREC, NDET, WF>(ev, P, 32 * w + lane, kThreads, dv, fv, fc);
+    chunk_total<PREC, NV>(dv, fv, fc, lane, ct[w]);
+  }
+  __syncwarp();
+}
+
+// Sums of one walker over the whole CTA: totals in `out` (shared), visible to every thread on
+// return; `ct` holds the warps' chunk totals.
+template <int PREC, int NDET, int WF>
+__device__ inline void cta_sums(const EventDev& ev, const WalkerParams& P, double (*ct)[NVals<NDET, WF>::value],
+                                double* out) {
   constexpr int NV = NVals<NDET, WF>::value;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double dv[NV];
   float fv[NV], fc[NV];
   partials<PREC, NDET, WF>(ev, P, threadIdx.x, kThreads, dv, fv, fc);
-  if (PREC == 0) {
-    warp_reduce_f64<NV>(dv);
-    if (lane == 0) for (int i = 0; i < NV; ++i) red[warp][i] = dv[i];
-  } else {
-    warp_reduce_f32<NV>(fv, fc);
-    if (lane == 0) for (int i = 0; i < NV; ++i) red[warp][i] = (double)fv[i] + (double)fc[i];
-  }
+  chunk_total<PREC, NV>(dv, fv, fc, lane, ct[warp]);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < NV; ++i) {
-      double t = 0.0;
-      for (int w = 0; w < kWarps; ++w) t += red[w][i];
-      out[i] = t;
-    }
-  }
+  if (threadIdx.x < NV) out[threadIdx.x] = chunks_sum<NV>(ct, threadIdx.x);
+  __syncthreads();
 }
 
 // ln L from reduced values laid out [det][re, im(, hh)]; the mixed paths' template-power sums
@@ -498,7 +554,7 @@ __global__ void __launch_bounds__(kThreads) likelihood_kernel(const EventDev* __
                                                                const double* __restrict__ theta, int n,
                                                                double* __restrict__ lnl, int32_t* status) {
   __shared__ WalkerParams P;
-  __shared__ double red[kWarps][kMaxVals];
+  __shared__ double red[kWarps][NVals<NDET, WF>::value];
   __shared__ double vals[kMaxVals];
   __shared__ int ok;
   const EventDev& ev = *evp;
@@ -545,7 +601,7 @@ __global__ void __launch_bounds__(kThreads) unit_likelihood_kernel(const EventDe
                                                                     const double* __restrict__ u, int n,
                                                                     double* __restrict__ lnl) {
   __shared__ WalkerParams P;
-  __shared__ double red[kWarps][kMaxVals];
+  __shared__ double red[kWarps][NVals<NDET, WF>::value];
   __shared__ double vals[kMaxVals];
   const EventDev& ev = *evp;
   const int w = blockIdx.x;
@@ -671,11 +727,10 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
   __shared__ int cstep[kSpecMax];
   __shared__ int mstep[32];
   __shared__ double lnl_p[kSpecMax];
-  __shared__ float part_sums[kSpecMax][2 * kMaxVals];
+  __shared__ double tot_p[kSpecMax][NV];
+  __shared__ double ct[kWarps][kWarps][NV];
   __shared__ double u[kMaxDim];
   __shared__ float u32[kMaxDim];
-  __shared__ double red[kWarps][kMaxVals];
-  __shared__ double vals[kMaxVals];
   __shared__ int wcount[kWarps];
   __shared__ int s_next, s_setup_warp, s_nin, s_end, s_needq;
   __shared__ int s_isflow[kSpecMax];
@@ -861,43 +916,29 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
     }
     __syncthreads();
     const int nin = s_nin;
-    // 2. likelihoods
+    // 2. likelihoods: the sums of proposal i into tot_p[i] (chunk totals in ct), then one lane
+    //    per proposal assembles ln L (the FP64 part runs once per proposal, on one warp)
     if (nin >= kWarps) {
-      // one warp per proposal; sums parked in shared memory, then one lane per proposal
-      // converts and assembles (the FP64 part runs once per proposal, on one warp)
+      // one warp per proposal, its four chunks in turn
       for (int i = warp; i < nin; i += kWarps) {
-        double dv[NV];
-        float fv[NV], fc[NV];
-        partials<PREC, NDET, WF>(ev, P[i], lane, 32, dv, fv, fc);
-        if (PREC == 0) {
-          warp_reduce_f64<NV>(dv);
-          if (lane == 0) lnl_p[i] = lnl_from_vals<PREC, NDET, WF>(ev, P[i], dv);
-        } else {
-          float rs, rc;
-          int q;
-          warp_halving_sums<NV>(fv, fc, lane, rs, rc, q);
-          // the lanes that ended with distinct indices (the lowest lane of each group) store
-          constexpr int V = Pow2Vals<NV>::value;
-          constexpr int group = 32 / V;
-          if ((lane & (group - 1)) == 0 && q < NV) { part_sums[i][2 * q] = rs; part_sums[i][2 * q + 1] = rc; }
-        }
-      }
-      if (PREC != 0) {
-        __syncthreads();
-        if (warp == sw && lane < nin) {
-          double v[NV];
-#pragma unroll
-          for (int q = 0; q < NV; ++q) v[q] = (double)part_sums[lane][2 * q] + (double)part_sums[lane][2 * q + 1];
-          lnl_p[lane] = lnl_from_vals<PREC, NDET, WF>(ev, P[lane], v);
-        }
+        warp_chunks<PREC, NDET, WF>(ev, P[i], lane, ct[warp]);
+        if (lane < NV) tot_p[i][lane] = chunks_sum<NV>(ct[warp], lane);
+        __syncwarp();
       }
     } else {
+      // fewer proposals than warps: the whole CTA on each in turn, chunk w on warp w
       for (int i = 0; i < nin; ++i) {
-        cta_sums<PREC, NDET, WF>(ev, P[i], red, vals);
-        if (threadIdx.x == 0) lnl_p[i] = lnl_from_vals<PREC, NDET, WF>(ev, P[i], vals);
+        double dv[NV];
+        float fv[NV], fc[NV];
+        partials<PREC, NDET, WF>(ev, P[i], threadIdx.x, kThreads, dv, fv, fc);
+        chunk_total<PREC, NV>(dv, fv, fc, lane, ct[0][warp]);
+        __syncthreads();
+        if (threadIdx.x < NV) tot_p[i][threadIdx.x] = chunks_sum<NV>(ct[0], threadIdx.x);
         __syncthreads();
       }
     }
+    __syncthreads();
+    if (warp == sw && lane < nin) lnl_p[lane] = lnl_from_vals<PREC, NDET, WF>(ev, P[lane], tot_p[lane]);
     __syncthreads();
     // 3. the steps in order
     if (threadIdx.x == 0) {
@@ -1306,7 +1347,7 @@ __global__ void __launch_bounds__(kThreads) hrss_kernel(const EventDev* __restri
                                                          const int32_t* __restrict__ blk_task,
                                                          const int32_t* __restrict__ blk_local) {
   __shared__ WalkerParams P;
-  __shared__ double red[kWarps][kMaxVals];
+  __shared__ double red[kWarps][NVals<NDET, WF>::value];
   __shared__ double vals[kMaxVals];
   __shared__ double x[kMaxDim], dvec[kMaxDim], pt[kMaxDim];
   __shared__ double s_rbl;
