@@ -399,6 +399,33 @@ def time_to_logz(gwns, device):
     return out
 
 
+def lnl_precision(gwns, w, ev, local, n=256):
+    """Worst ln L error of the mixed modes on the injection and n prior draws (the FP64 handle's
+    initial live points), measured against the FP64 mode, which the likelihood parity tests hold
+    within 1e-10 relative of the oracle's ln L.  Relative errors are taken against
+    max(|ln L|, SNR^2 / 2), the zero-noise floor of ln L near the truth."""
+    hs = {}
+    try:
+        for p in (synth.PREC_FP64, synth.PREC_MIXED, synth.PREC_MIXED_FF):
+            hs[p] = gwns.ns_init([gwns.make_config(w, synth.priors_with_injection(w, ev), precision=p)], [ev], local)
+        th, _ = gwns.ns_posterior(hs[synth.PREC_FP64], 0, cap=n)
+        th = np.ascontiguousarray(np.vstack([ev.theta_inj, th]))
+        lnl = {}
+        for p, h in hs.items():
+            lnl[p] = np.zeros(th.shape[0])
+            gwns.ns_likelihood_batch(h, 0, th, lnl[p])
+        ref = lnl[synth.PREC_FP64]
+        scale = np.maximum(np.abs(ref), 0.5 * w.snr ** 2)
+        out = {"points": int(th.shape[0]), "reference": "FP64 mode (within 1e-10 relative of the oracle)"}
+        for p, key in ((synth.PREC_MIXED, "mixed_fp64_phase"), (synth.PREC_MIXED_FF, "float_float")):
+            err = np.abs(lnl[p] - ref)
+            out[key] = {"max_abs": float(np.max(err)), "max_rel": float(np.max(err / scale))}
+        return out
+    finally:
+        for h in hs.values():
+            gwns.ns_free(h)
+
+
 def measure_workload(gwns, name, steps, warmup, rank, world, local, dist, flush, sample_clocks=True, p_flow=None,
                      with_fp64=True, cpu_seconds=10.0, pool=None, procs=1):
     """One workload's line: the float-float walk timed over `steps` sampler batches after
@@ -577,6 +604,7 @@ def measure_workload(gwns, name, steps, warmup, rank, world, local, dist, flush,
                              "spec_depth": plain["progress"]["spec_depth"]}
         out["mixed_fp64_phase"] = {"value": vm, "unit": UNIT, "ms_per_step": tm / steps}
         out["mixed_over_plain"] = value / vp
+    out["lnl_err_vs_fp64"] = lnl_precision(gwns, w, ev, local)
     if pool is not None:
         out["cpu_baseline"] = cpu_baseline(w, ev, cpu_seconds, pool, procs)
     return out
@@ -632,7 +660,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic"}
     for k in ("config", "plain_fp64", "mixed_fp64_phase", "mixed_over_plain", "p_flow", "p_flow_sweep",
               "speculative_evals_per_eval", "spec_depth", "mean_walk_steps", "mean_accept", "active_bins_per_eval",
-              "e2e", "gpu_launches", "roofline", "cpu_baseline"):
+              "e2e", "gpu_launches", "roofline", "lnl_err_vs_fp64", "cpu_baseline"):
         if k in head:
             line[k] = head[k]
     line["clocks"] = {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
