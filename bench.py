@@ -329,11 +329,12 @@ def run_to_logz(gwns, w, ev, precision, device, relbin_edges=None, **cfg_kw):
     try:
         if relbin_edges is not None:
             gwns.ns_relbin_set(h, 0, relbin_edges, ev.theta_inj)
-        done, batches = False, 0
+        done, batches, steps = False, 0, []
         while not done and batches < 4000:
             _, prog = gwns.ns_step(h, 8)
             batches += 8
             done = bool(prog[0]["done"])
+            steps.append(prog[0]["n_steps"])
         lz, lz_err, _, n_like = gwns.ns_evidence(h, 0)
         seconds = time.perf_counter() - t0
         _, lw = gwns.ns_posterior(h, 0)
@@ -344,17 +345,20 @@ def run_to_logz(gwns, w, ev, precision, device, relbin_edges=None, **cfg_kw):
     ess = float(1.0 / np.sum(wgt * wgt))
     return {"seconds": seconds, "log_z": lz, "log_z_err": lz_err, "n_like": int(n_like),
             "iterations": int(prog[0]["iterations"]), "done": done, "posterior_ess": ess,
-            "lnl_evals_per_ess": int(n_like) / ess}
+            "lnl_evals_per_ess": int(n_like) / ess, "walk_length_every_8_batches": steps}
 
 
-def flow_to_logz(gwns, w, ev, device, p_flows=(0.0, 0.5, 0.9)):
+def flow_to_logz(gwns, w, ev, device, p_flows=(0.0, 0.5, 0.9), weights=(1.0,)):
     """The learned-proposal configuration's metrics: time to ln Z and likelihood calls per
-    effective posterior sample, for the DE walk (p_flow 0) and the DE + flow walk, each run
-    from ns_init to its stopping rule in the float-float mode."""
+    effective posterior sample, for the DE walk (p_flow 0) and the DE + flow walk at each
+    weight of an accepted flow step in the walk-length retune (keys "p_flow" for weight 1,
+    "p_flow@w" otherwise), each run from ns_init to its stopping rule in the float-float mode."""
     out = {}
     for pf in p_flows:
-        kw = {} if pf == 0.0 else {"p_flow": pf, "flow_layers": 8}
-        out[str(pf)] = run_to_logz(gwns, w, ev, synth.PREC_MIXED_FF, device, **kw)
+        for wt in (weights if pf > 0.0 else (1.0,)):
+            kw = {} if pf == 0.0 else {"p_flow": pf, "flow_layers": 8, "flow_accept_weight": wt}
+            key = str(pf) if wt == 1.0 else f"{pf}@w{wt:g}"
+            out[key] = run_to_logz(gwns, w, ev, synth.PREC_MIXED_FF, device, **kw)
     return out
 
 
@@ -649,7 +653,8 @@ def run_ours(args):
         to_logz = time_to_logz(gwns, local) if args.workload == WORKLOAD else None
         if args.workload.endswith("_flow") and args.to_logz:
             ws, evs = build_events(args.workload, 0, local)
-            to_logz = flow_to_logz(gwns, ws[0], evs[0], local)
+            to_logz = flow_to_logz(gwns, ws[0], evs[0], local,
+                                   weights=tuple(float(x) for x in args.flow_weights.split(",")))
     finally:
         if pool is not None:
             pool.close()
@@ -806,6 +811,11 @@ def run_logz_convergence(args):
         arms = [("de_60_5000", {}, {}), ("de_240_50000", {"naccept": 240, "maxmcmc": 50000}, {}),
                 ("flow_0.5", {}, {"p_flow": 0.5, "flow_layers": 8}),
                 ("flow_0.9", {}, {"p_flow": 0.9, "flow_layers": 8}), ("hrss_198", {}, {"hrss_moves": 198})]
+        # and at each weight of an accepted flow step in the walk-length retune (--flow-weights)
+        for wt in (float(x) for x in args.flow_weights.split(",")):
+            if wt != 1.0:
+                arms += [(f"flow_{pf}_w{wt:g}", {}, {"p_flow": pf, "flow_layers": 8, "flow_accept_weight": wt})
+                         for pf in (0.5, 0.9)]
     out = {a[0]: [] for a in arms}
     for sd in range(args.logz_seeds):
         w0, ev = library_event(base, sd, local)
@@ -815,7 +825,8 @@ def run_logz_convergence(args):
             r = run_to_logz(gwns, replace(w0, **wk), ev, synth.PREC_MIXED_FF, local, relbin_edges=edges, **ck)
             out[tag].append(r)
             print(json.dumps({"seed": sd, "arm": tag, "log_z": r["log_z"], "log_z_err": r["log_z_err"],
-                              "seconds": r["seconds"], "n_like": r["n_like"], "iterations": r["iterations"]}),
+                              "seconds": r["seconds"], "n_like": r["n_like"], "iterations": r["iterations"],
+                              "walk_length_every_8_batches": r["walk_length_every_8_batches"]}),
                   file=sys.stderr, flush=True)
     ref = np.array([r["log_z"] for r in out["de_60_5000"]])
     summary = {}
@@ -966,6 +977,9 @@ def main():
     ap.add_argument("--p-flow", type=float, default=0.5, help="flow-step probability of the *_flow workloads")
     ap.add_argument("--to-logz", action="store_true",
                     help="*_flow workloads: also run p_flow 0, 0.5, 0.9 to their stopping rule (minutes)")
+    ap.add_argument("--flow-weights", default="1",
+                    help="--to-logz and --logz-convergence on *_flow workloads: comma-separated weights of "
+                         "an accepted flow step in the walk-length retune; the flow arms run at each")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCRIPTIONS),
                     help="bench workload (the default is the headline line)")
     ap.add_argument("--relbin", type=float, default=0.0,

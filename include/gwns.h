@@ -128,6 +128,15 @@ typedef struct ns_config {
                              walk-length retune; 0: 2 D).  Every event of a handle uses
                              HRSS or none does.  Needs n_live - num_delete > D.          */
     double flow_lr;       /* DE_FLOW: Adam learning rate (0: 3e-3)                  */
+    double flow_accept_weight; /* DE_FLOW: weight of an accepted flow step in the walk-length
+                             retune, in [1, 1e6] (0: 1).  The retune aims the batch mean of
+                             (accepted DE steps + w x accepted flow steps) at naccept: an
+                             accepted independence proposal moves a walker as far as w DE
+                             acceptances.  1 counts both kinds alike.  Weights above 1 are an
+                             experiment: they shorten the walks, and on an 11-parameter event
+                             they were measured to bias ln Z.  A handle with a weight other
+                             than 1 cannot use the batch-phase calls (ns_batch_*), which do
+                             not carry the flow acceptance counts.                       */
 } ns_config;
 
 /* One detector's data.  Pointers are HOST arrays of n_bins doubles, copied by ns_init. */
@@ -171,6 +180,8 @@ typedef struct ns_progress {
     int32_t spec_depth;   /* speculation depth of the next batch                    */
     int32_t spec_cap;     /* the cap on it in force (chosen by the autotuner when the
                              configuration leaves the depth automatic)                */
+    double mean_accept_flow; /* mean accepted flow steps per walker, last batch (of
+                             mean_accept)                                             */
 } ns_progress;
 
 typedef struct ns_handle ns_handle;

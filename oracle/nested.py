@@ -22,7 +22,10 @@ oracle.flow.init_flow and, in every batch it % flow_every == 0, after the deleti
 re-standardised and trained for flow_epochs full-batch Adam steps on the n_live - k
 survivors, which sample the prior above the new L* that the walks target (warm start:
 weights and Adam state persist); the walk then mixes flow steps with probability p_flow
-(oracle.walk).
+(oracle.walk).  With flow_accept_weight w (a reading: the paper gives no walk-length rule for
+flow steps), the retune of step 4 takes a = (sum of accepted steps + (w - 1) x sum of accepted
+flow steps) / k: an accepted independence proposal counts as w DE acceptances; w = 1 is the
+plain rule.
 With inner="hrss" the walkers instead make hrss_steps hit-and-run slice-sampling moves each
 (oracle.hrss; the inner kernel the paper names in Sec. 2.2 and Sec. 5) against the survivors,
 with the same starts, deletion and evidence; the move count is fixed (no retuning).
@@ -130,8 +133,8 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
                initial_u=None, n_steps0: int | None = None, replay_seed: int = 12345,
                p_flow: float = 0.0, flow_every: int = 1, flow_epochs: int = 50, flow_lr: float = 3e-3,
                flow_hidden: int = 128, flow_layers: int = 8, flow_bf16: bool = False,
-               inner: str = "de", hrss_steps: int = 0, walk_pool=None, walk_chunks: int = 1,
-               progress=None) -> NestedResult:
+               flow_accept_weight: float = 1.0, inner: str = "de", hrss_steps: int = 0, walk_pool=None,
+               walk_chunks: int = 1, progress=None) -> NestedResult:
     if inner not in ("de", "hrss"):
         raise ValueError("inner is 'de' or 'hrss'")
     k = num_delete
@@ -167,6 +170,7 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
         if flow is not None and it % flow_every == 0:
             flowmod.train(flow, u[surv], flow_epochs, adam, flow_bf16)
         starts = surv[start_indices(k, it, n_live - k, key)]
+        n_accf = np.zeros(k, dtype=np.int64)   # accepted flow steps per walker
         if inner == "hrss":
             n_steps = hrss_steps
             new_u, new_lnl, n_acc, n_call = hrss_walk(loglike, u[starts], lnl[starts], lnl_star, u[surv],
@@ -178,7 +182,7 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
         else:
             new_u, new_lnl, n_acc, n_call, _ = acceptance_walk(
                 loglike, u[starts], lnl[starts], lnl_star, u[surv], n_steps, periodic, key, it,
-                flow=flow, p_flow=p_flow, flow_bf16=flow_bf16)
+                flow=flow, p_flow=p_flow, flow_bf16=flow_bf16, flow_acc=n_accf)
         u[dead] = new_u
         lnl[dead] = new_lnl
         n_like += int(n_call.sum())
@@ -186,7 +190,8 @@ def run_nested(loglike, n_dim: int, n_live: int, num_delete: int, naccept: int, 
         stats.append((it, n_steps, mean_acc, int(n_call.sum()), lnl_star, log_z))
         if progress is not None:
             progress(stats[-1])
-        n_steps = retune(n_steps, mean_acc, naccept, delay_k, maxmcmc)
+        eff = (float(n_acc.sum()) + (flow_accept_weight - 1.0) * float(n_accf.sum())) / k
+        n_steps = retune(n_steps, eff, naccept, delay_k, maxmcmc)
         it += 1
         if term_kind == TERM_DLOGZ:
             if np.logaddexp(log_z, lnl.max() + log_x) - log_z < term_value:

@@ -47,10 +47,12 @@ def de_step_draws(t: int, walkers: np.ndarray, it: int, n_surv: int, n_dim: int,
 
 
 def acceptance_walk(loglike, u0, lnl0, lnl_star, survivors, n_steps, periodic, key, it,
-                    walker_ids=None, flow=None, p_flow=0.0, flow_bf16=False):
+                    walker_ids=None, flow=None, p_flow=0.0, flow_bf16=False, flow_acc=None):
     """Run the walk for every walker.  loglike(u [D]) -> float; survivors [n_s, D].
     The returned margin is, per walker, the smallest distance of any accept decision from
-    its threshold: |ln L(u') - ln L*| and, on flow steps, |ln U - (ln q(u) - ln q(u'))|."""
+    its threshold: |ln L(u') - ln L*| and, on flow steps, |ln U - (ln q(u) - ln q(u'))|.
+    flow_acc (an integer array [W], if given) receives each walker's accepted flow steps,
+    which n_acc includes."""
     u = np.array(u0, dtype=np.float64, copy=True)
     lnl = np.array(lnl0, dtype=np.float64, copy=True)
     W, D = u.shape
@@ -90,4 +92,6 @@ def acceptance_walk(loglike, u0, lnl0, lnl_star, survivors, n_steps, periodic, k
                 n_acc[w] += 1
                 if use_flow:
                     logq[w] = fq[w] if fstep[w] else flowmod.forward(flow, prop[w:w + 1], flow_bf16)[1][0]
+                    if fstep[w] and flow_acc is not None:
+                        flow_acc[w] += 1
     return u, lnl, n_acc, n_like, margin

@@ -25,6 +25,8 @@ struct Scratch {
 struct NsState {
   double log_x, log_z, lnl_star, dlogz, mean_accept, lnl_max, delay_k, term_value;
   double spec_mult, spec_p;   // speculation rule m = spec_mult / p; p of the last batch
+  double flow_w;              // weight of an accepted flow step in the walk-length retune
+  double mean_accept_flow;    // mean accepted flow steps per walker, last batch
   int64_t n_dead, n_like, iteration, max_iter, dead_cap, n_bins_eval, n_spec_eval;
   int32_t n_live, k, D, n_steps, naccept, maxmcmc, term_kind, done, zero_accept, overflow;
   int32_t spec, spec_auto, spec_cap, spec_rule;   // spec = min(spec_rule, spec_cap)
@@ -44,6 +46,7 @@ struct NsState {
   int32_t* slot;       // [k]
   int64_t* w_nb;       // [k] active bins evaluated per walker
   int64_t* w_ns;       // [k] likelihoods evaluated per walker, speculative ones included
+  int32_t* w_naf;      // [k] accepted flow steps per walker (of w_na)
   double* dead_u;      // [dead_cap][D]
   double* dead_lnl;    // [dead_cap]
   double* dead_logw;   // [dead_cap]

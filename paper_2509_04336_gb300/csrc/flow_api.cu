@@ -77,8 +77,14 @@ int check_err_flag(ns_handle* h, cudaStream_t s, const char* what) {
 int flow_check_config(const ns_config& c, int e) {
   if (c.proposal != NS_PROPOSAL_DE && c.proposal != NS_PROPOSAL_DE_FLOW && c.proposal != NS_PROPOSAL_HRSS)
     return set_error(nullptr, NS_EINVAL, "event %d: unknown proposal %d", e, c.proposal);
-  if (c.proposal != NS_PROPOSAL_DE_FLOW) return NS_OK;
+  const bool weight_set = c.flow_accept_weight != 0.0 && c.flow_accept_weight != 1.0;
+  if (c.proposal != NS_PROPOSAL_DE_FLOW) {
+    if (weight_set) return set_error(nullptr, NS_EINVAL, "event %d: flow_accept_weight is for NS_PROPOSAL_DE_FLOW", e);
+    return NS_OK;
+  }
   if (!(c.p_flow >= 0.0 && c.p_flow <= 1.0)) return set_error(nullptr, NS_EINVAL, "event %d: p_flow must be in [0, 1]", e);
+  if (c.flow_accept_weight != 0.0 && !(c.flow_accept_weight >= 1.0 && c.flow_accept_weight <= 1e6))
+    return set_error(nullptr, NS_EINVAL, "event %d: flow_accept_weight must be 0 or in [1, 1e6]", e);
   if (c.flow_layers < 0 || c.flow_layers > kFlowMaxLayers)
     return set_error(nullptr, NS_EINVAL, "event %d: flow_layers must be in 0..%d", e, kFlowMaxLayers);
   if (c.flow_every < 0 || c.flow_epochs < 0 || !(c.flow_lr >= 0.0) || !std::isfinite(c.flow_lr))

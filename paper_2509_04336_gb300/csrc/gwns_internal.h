@@ -24,6 +24,7 @@ struct WalkTask {
   int32_t* n_like;         // [n]
   int64_t* n_bins;         // [n] active bins evaluated per walker (may be null)
   int64_t* n_spec;         // [n] likelihoods evaluated speculatively, used or not (may be null)
+  int32_t* n_acc_flow;     // [n] accepted flow steps, of n_acc (may be null)
   double lnl_star;
   int64_t iteration;
   int64_t walker_offset;

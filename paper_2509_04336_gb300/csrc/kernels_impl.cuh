@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
     s_setup_warp = (int)(atomicAdd(&g_walk_sm_arrivals[smid & 255u], 1u) % (unsigned)kWarps);
   }
   double lnl = T.lnl0[j];
-  int n_acc = 0, n_like = 0;
+  int n_acc = 0, n_acc_flow = 0, n_like = 0;
   int64_t n_bins = 0, n_spec = 0;
   const uint64_t t0 = threadIdx.x == 0 ? global_ns() : 0ull;
   const double de_scale = 2.38 / sqrt(2.0 * (double)D);
@@ -953,8 +953,12 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
           ++n_acc;
           nxt = cstep[i] + 1;
           if (use_flow) {
-            if (s_isflow[i]) s_logq = s_lqf[i];
-            else s_needq = 1;
+            if (s_isflow[i]) {
+              s_logq = s_lqf[i];
+              ++n_acc_flow;
+            } else {
+              s_needq = 1;
+            }
           }
           break;
         }
@@ -978,6 +982,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel(const EventDev* __res
   if (threadIdx.x == 0) {
     T.lnl_out[j] = lnl;
     T.n_acc[j] = n_acc;
+    if (T.n_acc_flow) T.n_acc_flow[j] = n_acc_flow;
     T.n_like[j] = n_like;
     if (T.n_bins) T.n_bins[j] = n_bins;
     if (T.n_spec) T.n_spec[j] = n_spec;
@@ -1068,7 +1073,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   for (int d = 0; d < kMaxDim; ++d)
     if (d < D && ev.prior[ev.dim_param[d]].periodic) periodic |= 1u << d;
   double lnl = T.lnl0[j];
-  int n_acc = 0, n_like = 0;
+  int n_acc = 0, n_acc_flow = 0, n_like = 0;
   int64_t n_bins = 0, n_spec = 0;
   const uint64_t t0 = threadIdx.x == 0 ? global_ns() : 0ull;
   const ff de_scale = ff_from_double(2.38 / sqrt(2.0 * (double)D));
@@ -1295,8 +1300,12 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
           ++n_acc;
           nxt = cstep[c] + 1;
           if (use_flow) {
-            if (s_isflow[c]) s_logq = s_lqf[c];
-            else s_needq = 1;
+            if (s_isflow[c]) {
+              s_logq = s_lqf[c];
+              ++n_acc_flow;
+            } else {
+              s_needq = 1;
+            }
           }
         }
         if (walk_should_stop(T, t0, abort_flag)) {   // watchdog: end the walk after this round
@@ -1318,6 +1327,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   if (threadIdx.x == 0) {
     T.lnl_out[j] = lnl;
     T.n_acc[j] = n_acc;
+    if (T.n_acc_flow) T.n_acc_flow[j] = n_acc_flow;
     T.n_like[j] = n_like;
     if (T.n_bins) T.n_bins[j] = n_bins;
     if (T.n_spec) T.n_spec[j] = n_spec;

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
   NsState& S = states[blockIdx.x];
   if (S.done) return;
   const int k = S.k, D = S.D, n = S.n_live, tid = threadIdx.x;
-  double acc = 0.0, calls = 0.0, zero = 0.0, bins = 0.0, spec = 0.0;
+  double acc = 0.0, calls = 0.0, zero = 0.0, bins = 0.0, spec = 0.0, accf = 0.0;
   for (int j = tid; j < k; j += kSelThreads) {
     int s = S.slot[j];
     bins += (double)S.w_nb[j];
@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
     for (int d = 0; d < D; ++d) S.live_u[(size_t)s * D + d] = S.w_uo[(size_t)j * D + d];
     S.live_lnl[s] = S.w_lo[j];
     acc += (double)S.w_na[j];
+    accf += (double)S.w_naf[j];
     calls += (double)S.w_nl[j];
     zero += (S.w_na[j] == 0) ? 1.0 : 0.0;
   }
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
   const double n_zero = block_sum(zero, buf);
   const double tot_bins = block_sum(bins, buf);
   const double tot_spec = block_sum(spec, buf);
+  const double tot_accf = block_sum(accf, buf);
   __syncthreads();
   double mx = -INFINITY;
   for (int i = tid; i < n; i += kSelThreads) mx = fmax(mx, S.live_lnl[i]);
@@ -232,6 +234,7 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
   if (tid == 0) {
     double mean_acc = tot_acc / (double)k;
     S.mean_accept = mean_acc;
+    S.mean_accept_flow = tot_accf / (double)k;
     S.n_like += (int64_t)tot_calls;
     S.n_bins_eval += (int64_t)tot_bins;
     S.n_spec_eval += (int64_t)tot_spec;
@@ -247,10 +250,12 @@ __global__ void __launch_bounds__(kSelThreads) insert_kernel(NsState* states, Wa
       S.spec = min(S.spec_rule, S.spec_cap);
     }
     if (n_zero > 0.0) S.zero_accept = 1;
-    // walk-length retune (batch-scaled delay); HRSS keeps its fixed move count
+    // walk-length retune (batch-scaled delay) on the mean of accepted DE steps plus flow_w
+    // times accepted flow steps; HRSS keeps its fixed move count
     if (S.hrss == 0) {
       double ns = (double)S.n_steps;
-      double x = (S.delay_k * ns + ns * (double)S.naccept / fmax(mean_acc, 0.5)) / (S.delay_k + 1.0);
+      const double eff = (tot_acc + (S.flow_w - 1.0) * tot_accf) / (double)k;
+      double x = (S.delay_k * ns + ns * (double)S.naccept / fmax(eff, 0.5)) / (S.delay_k + 1.0);
       double r = floor(x + 0.5);
       r = fmin(fmax(r, 1.0), (double)S.maxmcmc);
       S.n_steps = (int32_t)r;
@@ -549,6 +554,7 @@ int nested_init(ns_handle* h) {
     S.spec = c.spec_depth > 0 ? c.spec_depth : (S.hrss ? hrss_default_spec(c.waveform) : 4);
     S.spec_mult = 1.4;
     S.spec_p = 0.0;
+    S.flow_w = c.flow_accept_weight > 0.0 ? c.flow_accept_weight : 1.0;
     const size_t n = S.n_live, k = S.k, D = S.D;
     if ((r = alloc(h, (void**)&S.live_u, sizeof(double) * n * D, "live_u")) ||
         (r = alloc(h, (void**)&S.live_lnl, sizeof(double) * n, "live_lnl")) ||
@@ -563,16 +569,20 @@ int nested_init(ns_handle* h) {
         (r = alloc(h, (void**)&S.slot, sizeof(int32_t) * k, "slot")) ||
         (r = alloc(h, (void**)&S.w_nb, sizeof(int64_t) * k, "w_nb")) ||
         (r = alloc(h, (void**)&S.w_ns, sizeof(int64_t) * k, "w_ns")) ||
+        (r = alloc(h, (void**)&S.w_naf, sizeof(int32_t) * k, "w_naf")) ||
         (r = alloc(h, (void**)&S.dead_u, sizeof(double) * S.dead_cap * D, "dead_u")) ||
         (r = alloc(h, (void**)&S.dead_lnl, sizeof(double) * S.dead_cap, "dead_lnl")) ||
         (r = alloc(h, (void**)&S.dead_logw, sizeof(double) * S.dead_cap, "dead_logw")) ||
         (r = alloc(h, (void**)&S.dead_nlive, sizeof(int32_t) * S.dead_cap, "dead_nlive")) ||
         (S.hrss && (r = alloc(h, (void**)&S.chol, sizeof(double) * D * D, "chol"))))
       return r;
+    // walks of the batch-phase calls fill only their own walker range
+    if (cudaError_t err = fill_on(h, S.w_naf, 0, sizeof(int32_t) * k)) return cuda_fail(h, err, "w_naf clear");
     WalkTask& T = tasks[e];
     std::memset(&T, 0, sizeof(T));
     T.surv = S.surv_u; T.survf = S.survf; T.u0 = S.w_u0; T.lnl0 = S.w_lnl0; T.u_out = S.w_uo; T.lnl_out = S.w_lo;
     T.n_acc = S.w_na; T.n_like = S.w_nl; T.n_bins = S.w_nb; T.n_spec = S.w_ns; T.spec = S.spec;
+    T.n_acc_flow = S.w_naf;
     T.lnl_star = -INFINITY; T.iteration = 0; T.walker_offset = 0;
     T.key0 = S.key0; T.key1 = S.key1; T.n_s = S.n_live - S.k; T.n = S.k; T.n_steps = S.n_steps;
     T.done = 0; T.event = e;
@@ -617,7 +627,7 @@ void nested_free(ns_handle* h) {
   for (auto& E : h->events) {
     NsState& S = E.ns;
     void* ptrs[] = {S.live_u, S.live_lnl, S.surv_u, S.survf, S.w_u0, S.w_lnl0, S.w_uo, S.w_lo, S.w_na, S.w_nl,
-                    S.slot, S.w_nb, S.w_ns, S.dead_u, S.dead_lnl, S.dead_logw, S.dead_nlive, S.chol};
+                    S.slot, S.w_nb, S.w_ns, S.w_naf, S.dead_u, S.dead_lnl, S.dead_logw, S.dead_nlive, S.chol};
     for (void* p : ptrs) cudaFree(p);
     std::memset(&S, 0, sizeof(S));
   }
@@ -647,6 +657,7 @@ static void fill_progress(ns_handle* h, ns_progress* p) {
     p[e].n_spec = S.n_spec_eval;
     p[e].spec_depth = S.spec;
     p[e].spec_cap = S.spec_cap;
+    p[e].mean_accept_flow = S.mean_accept_flow;
   }
 }
 
@@ -867,7 +878,7 @@ extern "C" int ns_posterior(ns_handle* h, int event, double* theta_out, double* 
 
 // ---------------------------------------------------------------- checkpoint / resume
 namespace {
-const char kMagic[8] = {'G', 'W', 'N', 'S', 'S', 'T', '0', '3'};
+const char kMagic[8] = {'G', 'W', 'N', 'S', 'S', 'T', '0', '4'};
 
 bool wr(FILE* f, const void* p, size_t n) { return fwrite(p, 1, n, f) == n; }
 bool rd(FILE* f, void* p, size_t n) { return fread(p, 1, n, f) == n; }
@@ -988,6 +999,10 @@ int batch_checks(ns_handle* h, bool want_open) {
 extern "C" int ns_batch_begin(ns_handle* h) {
   int r = batch_checks(h, false);
   if (r) return r;
+  for (const auto& E : h->events)
+    if (E.ns.flow_w != 1.0)
+      return set_error(h, NS_EINVAL, "the batch-phase calls need flow_accept_weight 1 (they do not carry flow "
+                                     "acceptance counts)");
   bool all_done = true;
   for (auto& S : h->host_ns) all_done = all_done && S.done;
   if (all_done) return set_error(h, NS_ESTATE, "every event has finished");

@@ -42,7 +42,8 @@ class ns_config(C.Structure):
                 ("precision", C.c_int32), ("waveform", C.c_int32), ("max_iter", C.c_int32),
                 ("n_steps0", C.c_int32), ("seed", C.c_uint64), ("spec_depth", C.c_int32), ("proposal", C.c_int32),
                 ("p_flow", C.c_double), ("flow_layers", C.c_int32), ("flow_every", C.c_int32),
-                ("flow_epochs", C.c_int32), ("hrss_moves", C.c_int32), ("flow_lr", C.c_double)]
+                ("flow_epochs", C.c_int32), ("hrss_moves", C.c_int32), ("flow_lr", C.c_double),
+                ("flow_accept_weight", C.c_double)]
 
 
 class ns_detector(C.Structure):
@@ -60,7 +61,7 @@ class ns_progress(C.Structure):
                 ("log_x", C.c_double), ("lnl_star", C.c_double), ("mean_accept", C.c_double),
                 ("n_steps", C.c_int32), ("done", C.c_int32), ("n_bins", C.c_int64), ("walk_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("n_spec", C.c_int64), ("spec_depth", C.c_int32),
-                ("spec_cap", C.c_int32)]
+                ("spec_cap", C.c_int32), ("mean_accept_flow", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -172,7 +173,7 @@ def _same_kind(*arrays):
 # ---------------------------------------------------------------- marshalling helpers
 def make_config(w: synth.Workload, priors=None, *, precision=None, max_iter=0, n_steps0=0, delay=-1.0,
                 seed=None, spec_depth=0, p_flow=None, flow_layers=0, flow_every=0, flow_epochs=0,
-                flow_lr=0.0, hrss_moves=None) -> ns_config:
+                flow_lr=0.0, hrss_moves=None, flow_accept_weight=0.0) -> ns_config:
     """ns_config of a workload; p_flow (not None) selects NS_PROPOSAL_DE_FLOW, hrss_moves (not
     None; 0 means 2 D) NS_PROPOSAL_HRSS."""
     c = ns_config()
@@ -192,6 +193,7 @@ def make_config(w: synth.Workload, priors=None, *, precision=None, max_iter=0, n
         c.proposal = NS_PROPOSAL_DE_FLOW
         c.p_flow = p_flow
         c.flow_layers, c.flow_every, c.flow_epochs, c.flow_lr = flow_layers, flow_every, flow_epochs, flow_lr
+        c.flow_accept_weight = flow_accept_weight
     if hrss_moves is not None:
         c.proposal = NS_PROPOSAL_HRSS
         c.hrss_moves = hrss_moves

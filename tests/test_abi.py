@@ -87,6 +87,11 @@ def _event_and_config():
     (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_DE_FLOW), setattr(c, "flow_lr", -1.0)), gwns.NS_EINVAL),
     (lambda c, e: setattr(c, "hrss_moves", 1), gwns.NS_EINVAL),            # HRSS moves without HRSS
     (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_HRSS), setattr(c, "hrss_moves", -1)), gwns.NS_EINVAL),
+    (lambda c, e: setattr(c, "flow_accept_weight", 10.0), gwns.NS_EINVAL),   # a flow weight without flow
+    (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_DE_FLOW), setattr(c, "flow_accept_weight", 0.5)),
+     gwns.NS_EINVAL),
+    (lambda c, e: (setattr(c, "proposal", gwns.NS_PROPOSAL_DE_FLOW), setattr(c, "flow_accept_weight", float("nan"))),
+     gwns.NS_EINVAL),
 ])
 def test_init_rejects_bad_input_without_device_work(lib, mutate, code):
     w, ev = _event_and_config()

@@ -144,3 +144,23 @@ def test_retune_rule():
     assert nested.retune(100, 30.0, 60, 0.0, 5000) == 200
     assert nested.retune(100, 0.0, 60, 0.0, 5000) == 5000
     assert nested.retune(3, 60.0, 60, 0.0, 5000) == 3
+
+
+def test_flow_accept_weight_is_a_rescaled_target_when_every_step_is_a_flow_step():
+    # With p_flow = 1 every accepted step is a flow step, so the weighted count w a of the
+    # retune equals a at the target naccept / w: weight 4 at naccept 12 runs the chain of
+    # weight 1 at naccept 3 (same delay and first walk length; the batch means stay above 1/2,
+    # where the clamp of the rule would tell the two apart).  A dropped or misplaced (w - 1)
+    # term, or flow acceptances not counted, changes the walk lengths and the chain.
+    ll, _ = gaussian([0.5, 0.5], 0.15)
+    kw = dict(delay=2.0, n_steps0=24, max_iter=4, p_flow=1.0, flow_epochs=5, flow_hidden=16, flow_layers=2)
+    a = nested.run_nested(ll, 2, 24, 12, 12, 500, np.zeros(2, bool), (3, 4), flow_accept_weight=4.0, **kw)
+    b = nested.run_nested(ll, 2, 24, 12, 3, 500, np.zeros(2, bool), (3, 4), **kw)
+    assert [s[2] for s in a.stats] == [s[2] for s in b.stats]
+    assert min(s[2] for s in a.stats) >= 0.5
+    assert [s[1] for s in a.stats] == [s[1] for s in b.stats]
+    assert len({s[1] for s in a.stats}) > 1                     # the walk length did move
+    assert a.log_z == b.log_z and np.array_equal(a.dead_u, b.dead_u)
+    # and weight 1 at naccept 12 walks longer (its count is a quarter of the weighted one)
+    c = nested.run_nested(ll, 2, 24, 12, 12, 500, np.zeros(2, bool), (3, 4), **kw)
+    assert c.stats[1][1] > a.stats[1][1]
