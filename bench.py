@@ -846,6 +846,72 @@ def run_logz_convergence(args):
     return 0
 
 
+def run_batched_logz(args):
+    """The batched form's wall time to ln Z against the plain FP64 walk at the same accuracy: the
+    first N events of the 64-event population (n_live reduced to --batched-n-live, num_delete
+    half of it, maxmcmc to --batched-maxmcmc, in every arm, so that the plain FP64 arm ends in
+    minutes), each sampled to its stopping rule
+    (1) all in one handle, float-float mode, (2) one handle at a time, float-float mode, and
+    (3) all in one handle with the plain FP64 walk; every event's ln Z in (1) against (3), over
+    the two runs' errors."""
+    import torch
+
+    from dataclasses import replace
+
+    from paper_2509_04336_gb300 import build, gwns
+
+    rank, world, local = rank_info()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    build.build()
+    gwns.load()
+    n, nl, mm = args.batched_logz, args.batched_n_live, args.batched_maxmcmc
+    ws, evs = build_events("batched64", 0, local)
+    ws = [replace(w, n_live=nl, num_delete=nl // 2, maxmcmc=mm) for w in ws[:n]]
+    evs = evs[:n]
+
+    def one_handle(precision):
+        cfgs = [gwns.make_config(w, synth.priors_with_injection(w, ev), precision=precision)
+                for w, ev in zip(ws, evs)]
+        keep = [gwns.make_event(ev) for ev in evs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = gwns.ns_init(cfgs, [k[0] for k in keep], local)
+        try:
+            done, batches = False, 0
+            while not done and batches < 4000:
+                _, prog = gwns.ns_step(h, 8, n)
+                batches += 8
+                done = all(p["done"] for p in prog)
+            out = [gwns.ns_evidence(h, e) for e in range(n)]
+            seconds = time.perf_counter() - t0
+        finally:
+            gwns.ns_free(h)
+        return {"seconds": seconds, "log_z": [o[0] for o in out], "log_z_err": [o[1] for o in out],
+                "n_like": int(sum(o[3] for o in out)), "iterations": [int(p["iterations"]) for p in prog]}
+
+    batched = one_handle(synth.PREC_MIXED_FF)
+    seq = [run_to_logz(gwns, w, ev, synth.PREC_MIXED_FF, local) for w, ev in zip(ws, evs)]
+    plain = one_handle(synth.PREC_FP64)
+    d = np.array(batched["log_z"]) - np.array(plain["log_z"])
+    sd = np.hypot(np.array(batched["log_z_err"]), np.array(plain["log_z_err"]))
+    print(json.dumps({
+        "metric": "wall time to ln Z of N events: batched float-float, one at a time, batched plain FP64",
+        "workload": f"the first {n} events of batched64 ({WORKLOAD_DESCRIPTIONS['batched64']}), n_live {nl}, "
+                    f"num_delete {nl // 2}, maxmcmc {mm} (every arm)",
+        "bins": [int(ev.n_bins) for ev in evs],
+        "batched_float_float": batched,
+        "one_at_a_time_float_float": {"seconds": sum(r["seconds"] for r in seq), "log_z": [r["log_z"] for r in seq],
+                                      "n_like": int(sum(r["n_like"] for r in seq))},
+        "batched_plain_fp64": plain,
+        "speedup_batched_ff_over_plain_fp64": plain["seconds"] / batched["seconds"],
+        "speedup_batched_ff_over_one_at_a_time": sum(r["seconds"] for r in seq) / batched["seconds"],
+        "delta_log_z_ff_minus_fp64": d.tolist(), "delta_over_error": (d / sd).tolist(),
+        "mean_delta": float(d.mean()), "stderr_mean_delta": float(d.std(ddof=1) / math.sqrt(n)) if n > 1 else None}))
+    return 0
+
+
 def run_profile_case(args):
     """A small case for profilers: N batches of the bench workload, no timing."""
     from paper_2509_04336_gb300 import build, gwns
@@ -990,6 +1056,11 @@ def main():
     ap.add_argument("--hrss-moves", type=int, default=0, help="HRSS moves per walker and batch (0: 2 D)")
     ap.add_argument("--logz-convergence", action="store_true",
                     help="with --logz-seeds N: ln Z of DE walks with longer walks and of HRSS with more moves")
+    ap.add_argument("--batched-logz", type=int, default=0,
+                    help="N > 0: wall time to ln Z of the first N events of batched64, batched and one at a "
+                         "time in float-float and batched in plain FP64, instead")
+    ap.add_argument("--batched-n-live", type=int, default=250, help="--batched-logz: live points per event")
+    ap.add_argument("--batched-maxmcmc", type=int, default=5000, help="--batched-logz: walk-length cap")
     ap.add_argument("--logz-seeds", type=int, default=0,
                     help="N > 0: run --workload to ln Z in float-float and plain FP64 on N seeds instead")
     args = ap.parse_args()
@@ -997,6 +1068,8 @@ def main():
         return run_profile_case(args)
     if args.logz_seeds > 0:
         return run_logz_convergence(args) if args.logz_convergence else run_logz_seeds(args)
+    if args.batched_logz > 0:
+        return run_batched_logz(args)
     if args.hrss:
         if args.workload == "batched64" or args.workload.endswith("_flow"):
             ap.error("--hrss runs a single-event DE workload")
