@@ -53,7 +53,7 @@ ALG_SFU_PER_WALKER_BIN = 6.0
 #   exact time-shift reduction (9), sincospi (20), complex multiply-accumulate (6), two Kahan
 #   updates (8): 114 + 3 * 43 = 243.  IMRPhenomD form: 3 basis terms (42), arctangent (~20),
 #   reduction (2), amplitude shape (~12), per detector 43 + template power (6): 76 + 3 * 49 = 223.
-EXEC_FP32_FLOPS_PER_WALKER_BIN = {synth.TAYLORF2: 243.0, synth.PHENOMD_FORM: 223.0}
+EXEC_FP32_FLOPS_PER_WALKER_BIN = {synth.TAYLORF2: 199.0, synth.PHENOMD_FORM: 179.0}
 # Plain FP64 walk: the same formula count carried in FP64 (its FP64 sincos not counted).
 FP64_ALG_FLOPS_PER_WALKER_BIN = {synth.TAYLORF2: 101.0, synth.PHENOMD_FORM: 122.0}
 FP32_PEAK_TFLOPS = 80.5      # GB300 FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
@@ -61,7 +61,7 @@ FP64_PEAK_TFLOPS = 1.259     # GB300 FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 G
 # DRAM bytes (read + write) of one walk launch, from one ncu capture of the current kernel
 # (walk_kernel_ff<3, WF>, batch 10 of the 4 s TaylorF2 workload and batch 3 of the 8 s
 # IMRPhenomD one); None for workloads without a capture of the current kernel.
-NCU_WALK_TRAFFIC_BYTES = {"bbh11_3det_4s_taylorf2": 247808 + 0, "bbh11_3det_8s_phenomd": 1725696 + 109312}
+NCU_WALK_TRAFFIC_BYTES = {"bbh11_3det_4s_taylorf2": 247296 + 0, "bbh11_3det_8s_phenomd": 1354240 + 156672}
 # Workloads measured beside the headline in the default run (their own roofline, baseline, e2e).
 EXTRA_WORKLOADS = ("bbh11_3det_8s_phenomd", "batched64")
 

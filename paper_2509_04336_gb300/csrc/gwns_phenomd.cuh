@@ -329,7 +329,7 @@ __device__ __forceinline__ void pd_accumulate_ff(const EventDev& ev, const Walke
     float ph = (r0 + p.sa[det]) + x + kf * p.sbl[det];
     ph = ph - rintf(ph);
     float s, c;
-    sincospif(2.0f * ph, &s, &c);
+    sincos_turn_sfu(ph, &s, &c);
     float2 z = ev.z32[(size_t)det * ev.n_bins + k];
     kahan_add(acc.re[det], acc.cre[det], amp * fmaf(z.x, c, z.y * s));
     kahan_add(acc.im[det], acc.cim[det], amp * fmaf(z.y, c, -z.x * s));

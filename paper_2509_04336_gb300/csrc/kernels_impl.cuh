@@ -434,7 +434,7 @@ __device__ double rb_lnl_warp(const EventDev& ev, const WalkerParams& P, int lan
         float ph = (r0 + P.sa[det]) + (kb - rintf(kb)) + kf * P.sbl[det];
         ph = ph - rintf(ph);
         float sn, cs;
-        sincospif(2.0f * ph, &sn, &cs);
+        sincos_turn_sfu(ph, &sn, &cs);
         // h f^(7/6) 2^70 = amp (K P) exp(-2 pi i ph)
         const float hre = amp * (P.kpf_re[det] * cs + P.kpf_im[det] * sn);
         const float him = amp * (P.kpf_im[det] * cs - P.kpf_re[det] * sn);
