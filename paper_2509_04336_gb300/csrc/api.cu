@@ -526,7 +526,7 @@ extern "C" int ns_walk_batch(ns_handle* h, int event, const double* live_u, int 
         (e = cudaMemcpyAsync(d_task, &T, sizeof(T), cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(d_be, maps.data(), sizeof(int32_t) * 2 * n, cudaMemcpyHostToDevice, s)))
       return cuda_fail(h, e, "H2D walk inputs");
-    if ((e = launch_walk(h->precision, h->waveform, E.n_det, h->d_events, d_task, d_be, d_bl, n, s)) != cudaSuccess)
+    if ((e = launch_walk(h->precision, h->waveform, E.n_det, h->d_events, d_task, d_be, d_bl, n, s, walk_extras(h, event))) != cudaSuccess)
       return cuda_fail(h, e, "walk launch");
     if ((e = cudaMemcpyAsync(u_out, d_uo, sizeof(double) * nu, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(lnl_out, d_lo, sizeof(double) * n, cudaMemcpyDeviceToHost, s)) ||
@@ -545,7 +545,7 @@ extern "C" int ns_walk_batch(ns_handle* h, int event, const double* live_u, int 
   stage.insert(stage.end(), (char*)maps.data(), (char*)maps.data() + sizeof(int32_t) * 2 * n);
   if ((e = cudaMemcpyAsync(d_task, stage.data(), stage.size(), cudaMemcpyHostToDevice, s)))
     return cuda_fail(h, e, "H2D walk task");
-  e = launch_walk(h->precision, h->waveform, E.n_det, h->d_events, d_task, d_be, d_bl, n, s);
+  e = launch_walk(h->precision, h->waveform, E.n_det, h->d_events, d_task, d_be, d_bl, n, s, walk_extras(h, event));
   return e == cudaSuccess ? NS_OK : cuda_fail(h, e, "walk launch");
 }
 
@@ -555,6 +555,17 @@ void watchdog_fields(ns_handle* h, WalkTask& T) {
   T.abort = h->d_status + 3;
   T.status = h->d_status + 2;
   T.budget_ns = h->budget_ns;
+}
+
+bool walk_extras(const ns_handle* h, int e) {
+  const EventHost& E = h->events[e];
+  return E.dev.rb_nb > 0 || (E.flow.enabled && E.flow.p_flow > 0.0);
+}
+
+bool walk_extras(const ns_handle* h) {
+  for (int e = 0; e < (int)h->events.size(); ++e)
+    if (walk_extras(h, e)) return true;
+  return false;
 }
 
 cudaError_t copy_on(ns_handle* h, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {

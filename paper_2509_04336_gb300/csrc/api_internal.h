@@ -126,6 +126,10 @@ int ensure_scratch(ns_handle* h, gwns::Scratch& s, size_t bytes);
 int nested_init(ns_handle* h);
 int default_spec(int precision);
 int hrss_default_spec(int waveform);
+// Whether a walk of event e (of any event of the handle) uses flow proposals or the
+// relative-binning likelihood: launch_walk's extras.
+bool walk_extras(const ns_handle* h, int e);
+bool walk_extras(const ns_handle* h);
 void nested_free(ns_handle* h);
 void relbin_free(gwns::EventHost& E);
 // flow proposal (flow_api.cu)

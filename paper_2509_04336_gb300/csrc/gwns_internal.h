@@ -72,8 +72,11 @@ cudaError_t launch_waveform(int waveform, int n_det, const EventDev* d_ev, const
 // n_steps moves; n_acc receives the moves made).
 cudaError_t launch_hrss(int precision, int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
                         const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s);
-// Block b walks walker blk_local[b] of task blk_task[b].
+// Block b walks walker blk_local[b] of task blk_task[b].  extras: some task of the launch uses
+// flow proposals or the relative-binning likelihood (false lets mode 2 run a walk kernel
+// compiled without those paths).
 cudaError_t launch_walk(int precision, int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
-                        const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s);
+                        const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s,
+                        bool extras);
 
 }  // namespace gwns

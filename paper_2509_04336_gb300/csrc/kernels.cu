@@ -11,7 +11,8 @@ cudaError_t launch_unit_likelihood_p(int waveform, int n_det, const EventDev* d_
                                      double* d_lnl, cudaStream_t s);
 template <int P>
 cudaError_t launch_walk_p(int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
-                          const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s);
+                          const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s,
+                          bool extras);
 template <int P>
 cudaError_t launch_hrss_p(int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
                           const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s);
@@ -33,11 +34,14 @@ cudaError_t launch_unit_likelihood(int precision, int waveform, int n_det, const
 }
 
 cudaError_t launch_walk(int precision, int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
-                        const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s) {
+                        const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s,
+                        bool extras) {
   if (n_blocks <= 0) return cudaSuccess;
-  if (precision == 0) return launch_walk_p<0>(waveform, n_det, d_evs, d_tasks, d_blk_task, d_blk_local, n_blocks, s);
-  if (precision == 1) return launch_walk_p<1>(waveform, n_det, d_evs, d_tasks, d_blk_task, d_blk_local, n_blocks, s);
-  return launch_walk_p<2>(waveform, n_det, d_evs, d_tasks, d_blk_task, d_blk_local, n_blocks, s);
+  if (precision == 0)
+    return launch_walk_p<0>(waveform, n_det, d_evs, d_tasks, d_blk_task, d_blk_local, n_blocks, s, extras);
+  if (precision == 1)
+    return launch_walk_p<1>(waveform, n_det, d_evs, d_tasks, d_blk_task, d_blk_local, n_blocks, s, extras);
+  return launch_walk_p<2>(waveform, n_det, d_evs, d_tasks, d_blk_task, d_blk_local, n_blocks, s, extras);
 }
 
 cudaError_t launch_hrss(int precision, int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,

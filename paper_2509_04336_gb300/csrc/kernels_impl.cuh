@@ -1021,7 +1021,7 @@ __device__ __forceinline__ ff ff_wrap_unit(ff x) {
 // phase takes as long for 1 or 5 proposals as for 4 or 8, and the padding only advances the
 // chain further.  The IMRPhenomD form (thousands of bins a proposal) runs each proposal on the
 // whole CTA instead.
-template <int NDET, int WF>
+template <int NDET, int WF, bool XF>
 __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __restrict__ evs, WalkTask* tasks,
                                                             const int32_t* __restrict__ blk_task,
                                                             const int32_t* __restrict__ blk_local) {
@@ -1079,7 +1079,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
   const ff de_scale = ff_from_double(2.38 / sqrt(2.0 * (double)D));
   __syncthreads();
   const int sw = s_setup_warp;
-  const bool use_flow = T.flow != nullptr && T.p_flow > 0.0;
+  const bool use_flow = XF && T.flow != nullptr && T.p_flow > 0.0;
   const double p_flow = T.p_flow;
   if (use_flow) {
     const float lq = flow_logq_cta(*T.flow, u, fscr);
@@ -1214,7 +1214,7 @@ __global__ void __launch_bounds__(kThreads, 4) walk_kernel_ff(const EventDev* __
     // 3. likelihoods
     constexpr int V = Pow2Vals<NV>::value;
     constexpr int group = 32 / V;
-    const bool rb = ev.rb_nb > 0;
+    const bool rb = XF && ev.rb_nb > 0;
     if (rb) {
       // relative binning (~10^2 coarse-bin edges a proposal): a warp per proposal
       for (int i = warp; i < nin; i += kWarps) {
@@ -1912,18 +1912,30 @@ cudaError_t launch_unit_likelihood_p(int waveform, int n_det, const EventDev* d_
   return cudaGetLastError();
 }
 
-// Mode 2 runs the float-float walk; modes 0 and 1 the FP64-recheck walk.
+// Mode 2 runs the float-float walk; modes 0 and 1 the FP64-recheck walk.  A TaylorF2 launch
+// whose tasks use neither flow proposals nor the relative-binning likelihood (extras false)
+// runs the float-float walk compiled without those paths (a smaller kernel: its round is
+// short and instruction fetch is among its first stalls).  Both properties of an event are
+// fixed before its first ns_step (ns_relbin_set is refused after it), so the sampler's
+// captured batch graphs keep a valid choice.
 template <int P, int N, int W>
 void launch_walk_one(int n_blocks, cudaStream_t s, const EventDev* d_evs, WalkTask* d_tasks,
-                     const int32_t* d_blk_task, const int32_t* d_blk_local) {
-  if constexpr (P == 2) walk_kernel_ff<N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local);
-  else walk_kernel<P, N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local);
+                     const int32_t* d_blk_task, const int32_t* d_blk_local, bool extras) {
+  if constexpr (P == 2) {
+    if (W == 0 && !extras)
+      walk_kernel_ff<N, W, false><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local);
+    else
+      walk_kernel_ff<N, W, true><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local);
+  } else {
+    walk_kernel<P, N, W><<<n_blocks, kThreads, 0, s>>>(d_evs, d_tasks, d_blk_task, d_blk_local);
+  }
 }
 
 template <int P>
 cudaError_t launch_walk_p(int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
-                          const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s) {
-#define GWNS_WALK(P_, N, W) launch_walk_one<P_, N, W>(n_blocks, s, d_evs, d_tasks, d_blk_task, d_blk_local)
+                          const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s,
+                          bool extras) {
+#define GWNS_WALK(P_, N, W) launch_walk_one<P_, N, W>(n_blocks, s, d_evs, d_tasks, d_blk_task, d_blk_local, extras)
   GWNS_DISPATCH_W(GWNS_WALK, P)
 #undef GWNS_WALK
   return cudaGetLastError();

@@ -480,7 +480,7 @@ int enqueue_batch(ns_handle* h, int b, int64_t* launches) {
                     h->n_walk_blocks, h->stream);
   } else {
     e = launch_walk(h->precision, h->waveform, h->max_det, h->d_events, h->d_tasks, h->d_blk_task, h->d_blk_local,
-                    h->n_walk_blocks, h->stream);
+                    h->n_walk_blocks, h->stream, walk_extras(h));
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "walk launch");
   if ((e = cudaEventRecordWithFlags(h->walk_events[2 * b + 1], h->stream, cudaEventRecordExternal)) != cudaSuccess)
@@ -1059,7 +1059,8 @@ extern "C" int ns_batch_walk(ns_handle* h, int64_t walker_begin, int64_t walker_
   }
   if ((e = cudaEventRecord(h->walk_events[0], h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
   e = h->hrss ? launch_hrss(h->precision, h->waveform, h->max_det, h->d_events, h->d_tasks, d_bt, d_bl, nb, h->stream)
-              : launch_walk(h->precision, h->waveform, h->max_det, h->d_events, h->d_tasks, d_bt, d_bl, nb, h->stream);
+              : launch_walk(h->precision, h->waveform, h->max_det, h->d_events, h->d_tasks, d_bt, d_bl, nb, h->stream,
+                            walk_extras(h));
   if (e != cudaSuccess) return cuda_fail(h, e, "walk launch");
   if ((e = cudaEventRecord(h->walk_events[1], h->stream)) != cudaSuccess) return cuda_fail(h, e, "event");
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "walk");

@@ -121,6 +121,6 @@ extern "C" int ns_walk_batch_noalloc(ns_handle* h, int event, const double* live
   WalkTask* d_task = (WalkTask*)scratch;
   const int32_t* d_bt = (const int32_t*)(scratch + kTaskBytes);
   const int32_t* d_bl = d_bt + kNoAllocMaxWalkers;
-  e = launch_walk(h->precision, h->waveform, E.n_det, h->d_events, d_task, d_bt, d_bl, n, s);
+  e = launch_walk(h->precision, h->waveform, E.n_det, h->d_events, d_task, d_bt, d_bl, n, s, walk_extras(h, event));
   return e == cudaSuccess ? NS_OK : cuda_fail(h, e, "walk launch");
 }

@@ -152,3 +152,30 @@ def test_relbin_sampler_evidence_matches_the_full_likelihood():
     (lz_f, err_f, _, _), (lz_r, err_r, _, _) = res["full"], res["relbin"]
     print("ln Z full", lz_f, "+-", err_f, "relbin", lz_r, "+-", err_r)
     assert abs(lz_f - lz_r) < 4.0 * np.hypot(err_f, err_r)
+
+
+def test_sampler_walks_take_the_relative_binning_path():
+    # The sampler's batch graph chooses its walk kernel by whether an event uses the
+    # relative-binning likelihood (a TaylorF2 float-float walk without flow or relative binning
+    # runs a kernel compiled without those paths).  With ns_relbin_set before the first batch
+    # the walks must evaluate the relative-binning likelihood: a call touches the ~35 coarse-bin
+    # edges below the cutoff and one coarse bin's grid bins, where the full likelihood touches
+    # every active bin (~190 on this event).  After a batch has run the call is refused.
+    w, ev = event("four_param_2det_taylorf2")
+    edges = relbin.default_edges(ev.f_min, ev.df, ev.n_bins, 0.25)
+    per_call = {}
+    for tag in ("full", "relbin"):
+        h = gwns.ns_init([gwns.make_config(w, priors(w, ev), precision=synth.PREC_MIXED_FF)], [ev])
+        try:
+            if tag == "relbin":
+                gwns.ns_relbin_set(h, 0, edges, ev.theta_inj)
+            _, p0 = gwns.ns_step(h, 1)
+            _, p1 = gwns.ns_step(h, 3)
+            per_call[tag] = (p1[0]["n_bins"] - p0[0]["n_bins"]) / (p1[0]["n_like"] - p0[0]["n_like"])
+            with pytest.raises(gwns.GwnsError) as e:
+                gwns.ns_relbin_set(h, 0, None if tag == "relbin" else edges, ev.theta_inj)
+            assert e.value.code == gwns.NS_EINVAL
+        finally:
+            gwns.ns_free(h)
+    print("bins per call", per_call)
+    assert per_call["relbin"] < 0.6 * per_call["full"]
