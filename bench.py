@@ -61,7 +61,7 @@ FP64_PEAK_TFLOPS = 1.259     # GB300 FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 G
 # DRAM bytes (read + write) of one walk launch, from one ncu capture of the current kernel
 # (walk_kernel_ff<3, WF>, batch 10 of the 4 s TaylorF2 workload and batch 3 of the 8 s
 # IMRPhenomD one); None for workloads without a capture of the current kernel.
-NCU_WALK_TRAFFIC_BYTES = {"bbh11_3det_4s_taylorf2": None, "bbh11_3det_8s_phenomd": 1354240 + 156672}
+NCU_WALK_TRAFFIC_BYTES = {"bbh11_3det_4s_taylorf2": 239360 + 0, "bbh11_3det_8s_phenomd": 1354240 + 156672}
 # Workloads measured beside the headline in the default run (their own roofline, baseline, e2e).
 EXTRA_WORKLOADS = ("bbh11_3det_8s_phenomd", "batched64")
 
