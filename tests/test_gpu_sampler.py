@@ -64,6 +64,29 @@ def test_sequential_mode_matches_oracle():
                                          nested.batch_delay(w.naccept - 1, 1), w.maxmcmc)
 
 
+def test_largest_live_set_matches_oracle():
+    # n_live at its limit (4096, sorted by one CTA in shared memory) with k = 2048 walkers: two
+    # whole batches against the oracle's run -- the deleted points in order, the likelihood calls
+    # and the evidence (naccept 2 keeps the oracle's ~36k calls to seconds).
+    w, ev, pri, ll = tiny()
+    w = replace(w, n_live=4096, num_delete=2048, naccept=2)
+    iters = 2
+    ref = oracle_run(w, pri, ll, max_iter=iters)
+    h = gwns.ns_init([gwns.make_config(w, pri, precision=synth.PREC_FP64, max_iter=iters)], [ev])
+    try:
+        code, prog = gwns.ns_step(h, iters)
+        th, lw = gwns.ns_posterior(h, 0)
+    finally:
+        gwns.ns_free(h)
+    p = prog[0]
+    nd = iters * w.num_delete
+    assert p["iterations"] == iters and p["n_like"] == ref.n_like
+    assert ref.dead_u.shape[0] == nd and th.shape[0] == nd + w.n_live
+    dead = np.stack([P.transform(u, pri) for u in ref.dead_u])
+    assert np.allclose(th[:nd], dead, rtol=1e-12, atol=1e-12)
+    assert abs(p["log_z"] - np.logaddexp.reduce(ref.dead_logw)) < 1e-9
+
+
 def test_batches_with_likelihood_ratio_match_oracle():
     # use_ratio (Sec. 4.1.1): the sampler runs on ln Lambda = ln L + <d|d>/2; eight batches
     # follow the oracle's own run (same deletions, walks and evidence, which differs from the
