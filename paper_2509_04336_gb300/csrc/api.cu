@@ -347,6 +347,10 @@ extern "C" int ns_init(const ns_config* cfg, const ns_event* ev, int n_events, i
     ns_free(h);
     return set_error(nullptr, NS_ECUDA, "stream: %s", cudaGetErrorString(e0));
   }
+  if ((e0 = turn_table_upload(h->stream)) != cudaSuccess) {
+    ns_free(h);
+    return set_error(nullptr, NS_ECUDA, "angle table: %s", cudaGetErrorString(e0));
+  }
   if ((e0 = cudaMalloc(&h->d_events, sizeof(EventDev) * n_events)) != cudaSuccess) {
     ns_free(h);
     return set_error(nullptr, NS_ENOMEM, "event table: %s", cudaGetErrorString(e0));

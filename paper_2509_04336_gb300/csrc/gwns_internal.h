@@ -72,6 +72,8 @@ cudaError_t launch_waveform(int waveform, int n_det, const EventDev* d_ev, const
 // n_steps moves; n_acc receives the moves made).
 cudaError_t launch_hrss(int precision, int waveform, int n_det, const EventDev* d_evs, WalkTask* d_tasks,
                         const int32_t* d_blk_task, const int32_t* d_blk_local, int n_blocks, cudaStream_t s);
+// Fills the FP64 path's angle table on the current device (before any FP64 likelihood runs).
+cudaError_t turn_table_upload(cudaStream_t s);
 // Block b walks walker blk_local[b] of task blk_task[b].  extras: some task of the launch uses
 // flow proposals or the relative-binning likelihood (false lets mode 2 run a walk kernel
 // compiled without those paths).

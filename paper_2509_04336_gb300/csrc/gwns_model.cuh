@@ -528,6 +528,30 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   s = t;
 }
 
+// (sin, cos)(2 pi k / 64), k = 0 .. 63: the table of sincos_phase_f64, filled by ns_init from
+// extended-precision host values (turn_table_upload).
+__device__ double2 g_turn_tab[64];
+
+// sin and cos of 2 pi ph for a phase ph in cycles (|64 ph| < 2^31), FP64, by angle addition:
+// ph = j / 64 + d with j the integer nearest 64 ph (rounded by adding 1.5 * 2^52, whose low word
+// then holds j) and d = ph - j / 64 exact (|d| <= 1/128); sin and cos of 2 pi j / 64 (j mod 64)
+// come from g_turn_tab, those of x = 2 pi d (|x| <= pi / 64) from their Taylor series to x^9 and
+// x^8, whose first omitted terms are below 1e-17 of the result.  The whole-cycle part of ph
+// drops out with j mod 64, so no separate reduction of ph is needed.
+__device__ __forceinline__ void sincos_phase_f64(double ph, double* s, double* c) {
+  const double big = fma(64.0, ph, 6755399441055744.0);
+  const int j = __double2loint(big) & 63;
+  const double jd = big - 6755399441055744.0;
+  const double d = fma(jd, -0.015625, ph);
+  const double x = d * 6.283185307179586;
+  const double x2 = x * x;
+  const double sp = fma(x * x2, fma(x2, fma(x2, fma(x2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0), x);
+  const double cp = fma(x2, fma(x2, fma(x2, fma(x2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
+  const double2 t = g_turn_tab[j];
+  *s = fma(t.x, cp, t.y * sp);
+  *c = fma(t.y, cp, -(t.x * sp));
+}
+
 // FP64 path: every operation in double precision.
 template <int NDET>
 __device__ __forceinline__ void bin_accumulate_f64(const EventDev& ev, const WalkerParams& p, int k,
@@ -540,11 +564,10 @@ __device__ __forceinline__ void bin_accumulate_f64(const EventDev& ev, const Wal
 #pragma unroll
   for (int det = 0; det < NDET; ++det) {
     double ph = fma(p.tau[det], f, phi);
-    double r = ph - rint(ph);
     double s, c;
-    sincospi(2.0 * r, &s, &c);
+    sincos_phase_f64(ph, &s, &c);
     double2 z = ev.z64[(size_t)det * ev.n_bins + k];
-    // z * exp(-2 pi i r) = (zr c + zi s) + i (zi c - zr s)
+    // z * exp(-2 pi i ph) = (zr c + zi s) + i (zi c - zr s)
     acc.re[det] += z.x * c + z.y * s;
     acc.im[det] += z.y * c - z.x * s;
   }

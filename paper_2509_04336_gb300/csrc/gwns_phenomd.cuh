@@ -229,9 +229,8 @@ __device__ __forceinline__ void pd_accumulate_f64(const EventDev& ev, const Walk
 #pragma unroll
   for (int det = 0; det < NDET; ++det) {
     double ph = fma(p.tau[det], f, phi);
-    double r = ph - rint(ph);
     double s, c;
-    sincospi(2.0 * r, &s, &c);
+    sincos_phase_f64(ph, &s, &c);
     double2 z = ev.z64[(size_t)det * ev.n_bins + k];
     acc.re[det] += amp * (z.x * c + z.y * s);
     acc.im[det] += amp * (z.y * c - z.x * s);
