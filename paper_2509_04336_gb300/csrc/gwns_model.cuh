@@ -567,9 +567,9 @@ __device__ __forceinline__ void bin_accumulate_f64(const EventDev& ev, const Wal
     double s, c;
     sincos_phase_f64(ph, &s, &c);
     double2 z = ev.z64[(size_t)det * ev.n_bins + k];
-    // z * exp(-2 pi i ph) = (zr c + zi s) + i (zi c - zr s)
-    acc.re[det] += z.x * c + z.y * s;
-    acc.im[det] += z.y * c - z.x * s;
+    // z * exp(-2 pi i ph) = (zr c + zi s) + i (zi c - zr s), accumulated by two FMAs each
+    acc.re[det] = fma(z.x, c, fma(z.y, s, acc.re[det]));
+    acc.im[det] = fma(z.y, c, fma(-z.x, s, acc.im[det]));
   }
 }
 

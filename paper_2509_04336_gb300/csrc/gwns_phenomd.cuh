@@ -226,15 +226,18 @@ __device__ __forceinline__ void pd_accumulate_f64(const EventDev& ev, const Walk
     phi += e.at_scale * atan((e.M * f - e.at_c) * e.at_inv);
   }
   const double amp = pd_amp_f64(e, k, f, g[4]);
+  const double amp2 = amp * amp;
 #pragma unroll
   for (int det = 0; det < NDET; ++det) {
     double ph = fma(p.tau[det], f, phi);
     double s, c;
     sincos_phase_f64(ph, &s, &c);
-    double2 z = ev.z64[(size_t)det * ev.n_bins + k];
-    acc.re[det] += amp * (z.x * c + z.y * s);
-    acc.im[det] += amp * (z.y * c - z.x * s);
-    acc.hh[det] += amp * amp * ev.gw64[(size_t)det * ev.n_bins + k];
+    const double2 z = ev.z64[(size_t)det * ev.n_bins + k];
+    const double ax = amp * z.x, ay = amp * z.y;
+    // amp z exp(-2 pi i ph), accumulated by two FMAs a component
+    acc.re[det] = fma(ax, c, fma(ay, s, acc.re[det]));
+    acc.im[det] = fma(ay, c, fma(-ax, s, acc.im[det]));
+    acc.hh[det] = fma(amp2, ev.gw64[(size_t)det * ev.n_bins + k], acc.hh[det]);
   }
 }
 
