@@ -528,25 +528,25 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   s = t;
 }
 
-// (sin, cos)(2 pi k / 64), k = 0 .. 63: the table of sincos_phase_f64, filled by ns_init from
+// (sin, cos)(2 pi k / 256), k = 0 .. 255: the table of sincos_phase_f64, filled by ns_init from
 // extended-precision host values (turn_table_upload).
-__device__ double2 g_turn_tab[64];
+__device__ double2 g_turn_tab[256];
 
-// sin and cos of 2 pi ph for a phase ph in cycles (|64 ph| < 2^31), FP64, by angle addition:
-// ph = j / 64 + d with j the integer nearest 64 ph (rounded by adding 1.5 * 2^52, whose low word
-// then holds j) and d = ph - j / 64 exact (|d| <= 1/128); sin and cos of 2 pi j / 64 (j mod 64)
-// come from g_turn_tab, those of x = 2 pi d (|x| <= pi / 64) from their Taylor series to x^9 and
-// x^8, whose first omitted terms are below 1e-17 of the result.  The whole-cycle part of ph
-// drops out with j mod 64, so no separate reduction of ph is needed.
+// sin and cos of 2 pi ph for a phase ph in cycles (|256 ph| < 2^31), FP64, by angle addition:
+// ph = j / 256 + d with j the integer nearest 256 ph (rounded by adding 1.5 * 2^52, whose low
+// word then holds j) and d = ph - j / 256 exact (|d| <= 1/512); sin and cos of 2 pi j / 256
+// (j mod 256) come from g_turn_tab, those of x = 2 pi d (|x| <= pi / 256) from their Taylor
+// series to x^7 and x^6, whose first omitted terms are below 1e-20 of the result.  The
+// whole-cycle part of ph drops out with j mod 256, so no separate reduction of ph is needed.
 __device__ __forceinline__ void sincos_phase_f64(double ph, double* s, double* c) {
-  const double big = fma(64.0, ph, 6755399441055744.0);
-  const int j = __double2loint(big) & 63;
+  const double big = fma(256.0, ph, 6755399441055744.0);
+  const int j = __double2loint(big) & 255;
   const double jd = big - 6755399441055744.0;
-  const double d = fma(jd, -0.015625, ph);
+  const double d = fma(jd, -0.00390625, ph);
   const double x = d * 6.283185307179586;
   const double x2 = x * x;
-  const double sp = fma(x * x2, fma(x2, fma(x2, fma(x2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0), x);
-  const double cp = fma(x2, fma(x2, fma(x2, fma(x2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
+  const double sp = fma(x * x2, fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), x);
+  const double cp = fma(x2, fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
   const double2 t = g_turn_tab[j];
   *s = fma(t.x, cp, t.y * sp);
   *c = fma(t.y, cp, -(t.x * sp));

@@ -31,13 +31,13 @@ cudaError_t launch_waveform(int waveform, int n_det, const EventDev* d_ev, const
   return cudaGetLastError();
 }
 
-// The FP64 path's angle table (sincos_phase_f64): (sin, cos)(2 pi k / 64) from long-double host
+// The FP64 path's angle table (sincos_phase_f64): (sin, cos)(2 pi k / 256) from long-double host
 // values, into this translation unit's copy of g_turn_tab, which its kernels read.
 cudaError_t turn_table_upload(cudaStream_t s) {
-  double2 t[64];
+  double2 t[256];
   const long double two_pi = 6.283185307179586476925286766559005768L;
-  for (int k = 0; k < 64; ++k) {
-    const long double a = two_pi * (long double)k / 64.0L;
+  for (int k = 0; k < 256; ++k) {
+    const long double a = two_pi * (long double)k / 256.0L;
     t[k] = make_double2((double)sinl(a), (double)cosl(a));
   }
   void* p = nullptr;
